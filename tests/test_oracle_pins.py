@@ -1,0 +1,233 @@
+"""Pins for the CPU oracle (oracle/) against what the paper and mathematics fix.
+
+* brute force: every bond mask of small multigraphs (<= 12 bonds, self-loops
+  and duplicate entries included) against scipy's connected components;
+* hand-worked examples of the four steps of Section 3 (tests/golden);
+* the forest identity: on a tree, clusters = sites - open bonds, exactly;
+* the empty residual lists of a centre-numbered Bethe lattice (Section 4);
+* the renaming invariance of a Bethe lattice stored in random position;
+* the mean size of the centre cluster of a branching process;
+* crossings of the spanning probability near p_c = 1 - 2 sin(pi/18)
+  (honeycomb) and 2 sin(pi/18) (triangle), Section 4, Figs. 5-6.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy.sparse.csgraph import connected_components
+
+import lattices as L
+import oracle
+from oracle import stats
+from conftest import load_golden
+
+
+def _canonical_from_components(comp: np.ndarray) -> np.ndarray:
+    """Smallest member of each component, by first occurrence in site order."""
+    _, first = np.unique(comp, return_index=True)
+    rep = np.empty(comp.max() + 1 if comp.size else 0, np.int64)
+    rep[comp[first]] = first
+    return rep[comp].astype(np.int32)
+
+
+def _scipy_labels(n, edges_open):
+    if n == 0:
+        return np.zeros(0, np.int32)
+    u = np.array([a for a, b in edges_open] or [0], np.int64)
+    v = np.array([b for a, b in edges_open] or [0], np.int64)
+    w = np.ones(len(edges_open) or 1)
+    if not edges_open:
+        w[:] = 0
+    A = sp.coo_matrix((w, (u, v)), shape=(n, n)).tocsr()
+    A.eliminate_zeros()
+    _, comp = connected_components(A, directed=False)
+    return _canonical_from_components(comp)
+
+
+def _lattice_from_entries(n, rows_entries):
+    """rows_entries[i] = list of (j, bit); returns a lattices.Lattice."""
+    row_ptr = np.zeros(n + 1, np.int32)
+    cols, bitv = [], []
+    for i in range(n):
+        for j, b in rows_entries[i]:
+            cols.append(j); bitv.append(b)
+        row_ptr[i + 1] = len(cols)
+    ci = np.array(cols, np.int32)
+    return L.Lattice("test", n, len(cols), row_ptr, ci, L.pack_bits(np.array(bitv, bool)), 0.0, 0)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_bruteforce_all_masks(seed):
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(1, 9))
+    m = int(rng.integers(0, 13))
+    u = rng.integers(0, n, m)
+    v = rng.integers(0, n, m)
+    if seed % 3 == 0 and m >= 2:          # force a duplicate edge
+        u[1], v[1] = v[0], u[0]
+    # CSR listing each edge in both rows; bit of edge t in both copies
+    entries = [[] for _ in range(n)]
+    for t in range(m):
+        a, b = int(u[t]), int(v[t])
+        entries[a].append([b, 0, t]); entries[b].append([a, 0, t])
+    for mask in range(1 << m):
+        rows = [[(j, (mask >> t) & 1) for j, _, t in entries[i]] for i in range(n)]
+        lat = _lattice_from_entries(n, rows)
+        expect = _scipy_labels(n, [(int(u[t]), int(v[t])) for t in range(m) if (mask >> t) & 1])
+        o1 = oracle.uf_label(lat)
+        o2 = oracle.bfs_label(lat)
+        o3 = oracle.steps_label(lat)["label"]
+        assert np.array_equal(o1, expect), (mask, o1, expect)
+        assert np.array_equal(o2, expect)
+        assert np.array_equal(o3, expect)
+
+
+@pytest.mark.parametrize("name", ["worked_example.txt", "row_max_rule.txt", "duplicate_min.txt"])
+def test_golden_steps(name):
+    g = load_golden(name)
+    n = g["n"][0]
+    rp = np.array(g["row_ptr"], np.int32)
+    lat = L.Lattice("golden", n, int(rp[-1]), rp, np.array(g["col_idx"], np.int32),
+                    L.pack_bits(np.array(g["open"], bool)), 0.0, 0)
+    st = oracle.steps_label(lat)
+    assert st["after_init"].tolist() == g["after_init"]
+    assert st["after_ii"].tolist() == g["after_ii"]
+    assert st["after_iii"].tolist() == g["after_iii"]
+    assert st["label"].tolist() == g["label"]
+    res = g.get("residual", {})
+    for i in range(n):
+        assert st["residual"][i].tolist() == res.get(i, []), i
+    assert st["n_residual"] == sum(len(v) for v in res.values())
+    assert oracle.uf_label(lat).tolist() == g["label"]
+    assert oracle.bfs_label(lat).tolist() == g["label"]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_graphs_agree_and_invariants(seed):
+    lat = L.random_graph(3000, 4000, seed, asymmetric=0.3 if seed % 2 else 0.0, p=0.55)
+    o1, o2, o3 = oracle.uf_label(lat), oracle.bfs_label(lat), oracle.steps_label(lat)["label"]
+    assert np.array_equal(o1, o2) and np.array_equal(o1, o3)
+    # the bond set read from row max(i, j): the generator's per-edge state
+    u, v = lat.meta["edges"]
+    op = lat.meta["open"]
+    keep = op & (u != v)
+    expect = _scipy_labels(lat.n, list(zip(u[keep].tolist(), v[keep].tolist())))
+    assert np.array_equal(o1, expect)
+    idx = np.arange(lat.n)
+    assert np.all(o1 <= idx) and np.array_equal(o1[o1], o1)
+
+
+@pytest.mark.parametrize("z,S,p,perm", [(3, 8, 0.5, None), (3, 8, 0.5, 9), (4, 6, 0.4, 5),
+                                        (6, 4, 0.9, 2), (3, 10, 1.0, 1), (5, 5, 0.0, None)])
+def test_tree_identity(z, S, p, perm):
+    """On a forest every open bond joins two clusters: clusters = N - open bonds."""
+    for seed in range(3):
+        lat = L.cayley(z, S, p, 100 + seed, perm_seed=perm)
+        lab = oracle.uf_label(lat)
+        assert stats.n_clusters(lab) == lat.n - lat.n_open_bonds
+        assert np.array_equal(lab, oracle.bfs_label(lat))
+
+
+@pytest.mark.parametrize("z,S", [(3, 9), (4, 6), (6, 4)])
+@pytest.mark.parametrize("p", [0.25, 0.5, 1.0])
+def test_standard_position_has_empty_residual_lists(z, S, p):
+    """Section 4: numbered from the centre, every site has at most one lower
+    neighbour (its parent), so no residual list survives step (i)."""
+    lat = L.cayley(z, S, p, 7)
+    st = oracle.steps_label(lat)
+    assert st["n_residual"] == 0
+    rnd = L.cayley(z, S, 1.0, 7, perm_seed=3)
+    assert oracle.steps_label(rnd)["n_residual"] > 0
+
+
+def test_random_position_is_a_renaming():
+    std = L.cayley(3, 9, 0.55, 21)
+    rnd = L.cayley(3, 9, 0.55, 21, perm_seed=77)
+    P = rnd.meta["perm"]
+    a, b = oracle.uf_label(std), oracle.uf_label(rnd)
+    # same partition after renaming: sites s, t together in std iff P[s], P[t] together in rnd
+    ren = b[P]                                  # label (in rnd numbering) of standard site s
+    # each std cluster maps to exactly one rnd cluster and vice versa
+    m1 = {}
+    for s in range(std.n):
+        m1.setdefault(int(a[s]), set()).add(int(ren[s]))
+    assert all(len(v) == 1 for v in m1.values())
+    assert len({next(iter(v)) for v in m1.values()}) == len(m1)
+
+
+def _bethe_center_closed_form(z, S, p):
+    # Each of the z (z-1)^(k-1) sites of shell k joins the centre's cluster iff
+    # the k bonds of its path to the centre are open (a branching process).
+    return 1.0 + z * sum(p ** k * (z - 1) ** (k - 1) for k in range(1, S + 1))
+
+
+@pytest.mark.parametrize("z,S,p", [(3, 10, 0.5), (4, 7, 0.25), (3, 8, 0.7), (5, 5, 0.25)])
+def test_bethe_center_cluster_mean(z, S, p):
+    """p_c = 1/(z-1) for the Bethe lattice (Section 4): at p_c the mean centre
+    cluster grows linearly with the shell count; the Monte Carlo mean of the
+    oracle's cluster sizes must match the branching-process expectation."""
+    sizes = []
+    for seed in range(1500):
+        perm = seed if seed % 2 else None
+        lat = L.cayley(z, S, p, 5000 + seed, perm_seed=perm)
+        lab = oracle.uf_label(lat)
+        c = L.cayley_center(lat)
+        sizes.append(int(np.count_nonzero(lab == lab[c])))
+    sizes = np.array(sizes, float)
+    mean, sd = sizes.mean(), sizes.std(ddof=1)
+    expect = _bethe_center_closed_form(z, S, p)
+    assert abs(mean - expect) < 5 * sd / math.sqrt(sizes.size), (mean, expect)
+    if abs(p - 1 / (z - 1)) < 1e-12:
+        assert abs(expect - (1 + z * S / (z - 1))) < 1e-9
+
+
+def _span_prob(make, Ls, p, samples, seed0):
+    hits = 0
+    for s in range(samples):
+        lat = make(Ls, p, seed0 + s)
+        lab = oracle.uf_label(lat)
+        if stats.spans(lab, L.row_sites(lat, 0), L.row_sites(lat, Ls - 1)):
+            hits += 1
+    return hits / samples
+
+
+@pytest.mark.parametrize("kind", ["triangle", "honeycomb"])
+def test_spanning_crossing_brackets_pc(kind):
+    """R_span(p) curves of different sizes cross at p_c (Section 4): below p_c the
+    larger system spans less often, above it more often."""
+    pc = L.PC_TRIANGLE if kind == "triangle" else L.PC_HONEYCOMB
+    make = (lambda Ls, p, s: L.triangle(Ls, p, s, periodic_y=False)) if kind == "triangle" else \
+           (lambda Ls, p, s: L.honeycomb(Ls, p, s, periodic_y=False))
+    n = 500
+    d = 0.04
+    lo_s, lo_b = _span_prob(make, 12, pc - d, n, 1), _span_prob(make, 64, pc - d, n, 2)
+    hi_s, hi_b = _span_prob(make, 12, pc + d, n, 3), _span_prob(make, 64, pc + d, n, 4)
+    def tol(a, b):   # 4 standard errors of a difference of two binomial proportions
+        return 4 * math.sqrt((a * (1 - a) + b * (1 - b)) / n + 1.0 / n ** 2)
+    assert lo_s - lo_b > tol(lo_s, lo_b), (lo_s, lo_b)
+    assert hi_b - hi_s > tol(hi_s, hi_b), (hi_s, hi_b)
+
+
+def test_extremes():
+    tri = L.triangle(16, 0.0, 1)
+    assert np.array_equal(oracle.uf_label(tri), np.arange(tri.n))
+    tri = L.triangle(16, 1.0, 1)
+    assert not oracle.uf_label(tri).any()
+    empty = L.Lattice("empty", 0, 0, np.zeros(1, np.int32), np.zeros(0, np.int32),
+                      np.zeros(1, np.uint32), 0.0, 0)
+    assert oracle.uf_label(empty).size == 0
+    bad = L.Lattice("bad", 2, 1, np.array([0, 1, 1], np.int32), np.array([5], np.int32),
+                    np.zeros(1, np.uint32), 0.0, 0)
+    with pytest.raises(ValueError):
+        oracle.uf_label(bad)
+
+
+def test_batched_oracle_matches_single():
+    specs = [dict(kind="honeycomb", L=9, p=0.65, seed=1), dict(kind="cayley", z=4, shells=5, p=0.33,
+             seed=2, perm_seed=3), dict(kind="triangle", L=11, p=0.35, seed=4)]
+    b = L.make_batch(specs)
+    lab = oracle.uf_label_batched(b)
+    for k in range(b.k):
+        s0, s1 = b.site_off[k], b.site_off[k + 1]
+        assert np.array_equal(lab[s0:s1], oracle.bfs_label(b.instance(k)))
