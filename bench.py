@@ -1,0 +1,402 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 cluster-labelling path (Komura's generalized GPU CCL).
+
+One step = one pass of the four labelling steps (init, analysis, label
+reduction, analysis) over one instance of the workload, inputs resident in
+HBM. Default workload: triangle-lattice bond percolation, 4096 x 4096 sites
+(16,777,216 sites, 100,663,296 CSR entries), periodic, p = 0.3473, seed 2.
+
+Prints one JSON line (rank 0): sites labelled per second over all ranks,
+the roofline of the dominant kernel, the CPU oracle baseline, the end-to-end
+figure through the host-buffer entry point, and the clocks seen meanwhile.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config NAME] [--impl ours|reference]
+
+Multi-GPU (torchrun): replicas only -- every rank labels its own seeded
+instance, with no collective on the data path; ranks meet at barriers around
+the timed region and the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import math
+import os
+import statistics
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import lattices as L  # noqa: E402
+
+CONFIGS = {
+    "tri4096": dict(kind="triangle", L=4096, p=0.3473, seed=2,
+                    desc="triangle bond percolation 4096x4096 periodic p=0.3473"),
+    "hc256": dict(kind="honeycomb", L=256, p=0.6527, seed=1,
+                  desc="honeycomb bond percolation 256x256 cells periodic p=0.6527"),
+    "bethe24": dict(kind="cayley", z=3, shells=24, p=0.5, seed=3, perm_seed=3,
+                    desc="Bethe lattice z=3, 24 shells, random position, p=0.5"),
+    "tri16384": dict(kind="triangle", L=16384, p=0.3473, seed=5,
+                     desc="triangle bond percolation 16384x16384 periodic p=0.3473"),
+}
+L2_BYTES = 129 * 1024 * 1024
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region: NVML through ctypes (read-only queries)
+
+class ClockSampler:
+    REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+               0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+               0x100: "display_clock_setting"}
+
+    def __init__(self, index: int, uuid: str | None = None):
+        self.samples, self.reasons, self.max_mhz = [], 0, None
+        self._stop = threading.Event()
+        self._th = None
+        try:
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit failed")
+            h = ctypes.c_void_p()
+            found = False
+            if uuid:
+                u = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+                found = nv.nvmlDeviceGetHandleByUUID(u.encode(), ctypes.byref(h)) == 0
+            if not found and nv.nvmlDeviceGetHandleByIndex_v2(index, ctypes.byref(h)) != 0:
+                raise OSError("no handle")
+            self.nv, self.h = nv, h
+            mx = ctypes.c_uint()
+            if nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:   # NVML_CLOCK_SM = 1
+                self.max_mhz = int(mx.value)
+        except OSError:
+            self.nv = None
+
+    def _run(self):
+        clk, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        fn = getattr(self.nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self._stop.is_set():
+            if self.nv.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(clk)) == 0:
+                self.samples.append(int(clk.value))
+            if fn(self.h, ctypes.byref(rs)) == 0:
+                self.reasons |= int(rs.value)
+            time.sleep(0.001)
+
+    def start(self):
+        if self.nv is not None:
+            self._th = threading.Thread(target=self._run, daemon=True)
+            self._th.start()
+
+    def stop(self):
+        if self._th is not None:
+            self._stop.set()
+            self._th.join()
+        names = [v for k, v in self.REASONS.items() if self.reasons & k and k != 0x1]
+        return {"sm_mhz": statistics.median(self.samples) if self.samples else None,
+                "sm_max_mhz": self.max_mhz, "reasons": names, "samples": len(self.samples),
+                "source": "nvml" if self.nv is not None else "unavailable"}
+
+
+# ----------------------------------------------------------------------------
+# oracle timing (CPU baseline / reference arm)
+
+def oracle_time(lat, budget_s: float, min_reps: int = 1):
+    """Times the oracle's union-find labelling of the full instance on one core,
+    repeating until `budget_s` seconds have elapsed; returns (sites/s, reps, secs)."""
+    import oracle
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.uf_label(lat)
+        reps += 1
+        el = time.perf_counter() - t0
+        if reps >= min_reps and el >= budget_s:
+            break
+    return lat.n * reps / el, reps, el
+
+
+def make_workload(name: str, rank: int):
+    c = dict(CONFIGS[name])
+    desc = c.pop("desc")
+    c["seed"] = c["seed"] + 1000 * rank      # replicas: one seeded instance per rank
+    if "perm_seed" in c:
+        c["perm_seed"] = c["perm_seed"] + 1000 * rank
+    return L.make_instance(c), desc
+
+
+def algorithmic_bytes(n: int, nnz: int, q: int) -> dict:
+    """Minimum bytes each step must move (each array read or written once).
+
+    init:     row_ptr 4(n+1) + col_idx 4 nnz + bit words 4 ceil(nnz/32) + labels 4n
+              + residual pairs 8q + chunk records 16 ceil(n/32)
+    analysis: labels read 4n + write 4n (each of steps ii and iv)
+    reduce:   chunk records 16 ceil(n/32) + pairs 8q + two label reads 8q
+    """
+    chunks = (n + 31) // 32
+    b_init = 4 * (n + 1) + 4 * nnz + 4 * ((nnz + 31) // 32) + 4 * n + 8 * q + 16 * chunks
+    b_ana = 8 * n
+    b_red = 16 * chunks + 16 * q
+    return {"init": b_init, "analysis_ii": b_ana, "reduce": b_red, "analysis_iv": b_ana,
+            "path": b_init + 2 * b_ana + b_red}
+
+
+def _source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1603_08357_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_1603_08357_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources (same hash); else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        ent = rec.get(f"{kernel}:{workload}")
+        if ent and ent.get("source_hash") == _source_hash():
+            return float(ent["dram_bytes_per_launch"]), ent.get("scaled_from")
+    except Exception:
+        pass
+    return None, None
+
+
+# ----------------------------------------------------------------------------
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    lat, desc = make_workload(args.config, 0)
+    import oracle  # noqa: F401
+    per_step = []
+    for _ in range(args.warmup):
+        oracle_time(lat, 0.0)
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_time(lat, 0.0)
+        per_step.append(time.perf_counter() - t0)
+    wall = time.perf_counter() - t_all
+    ms = 1e3 * wall / args.steps
+    value = lat.n / (ms / 1e3)
+    line = {
+        "impl": "reference", "metric": "sites labeled/s", "value": value, "unit": "sites/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": args.config, "desc": desc, "n_sites": lat.n, "nnz": lat.nnz,
+                   "l2": "inputs larger than L2 (no flush)" if lat.nnz * 4 > L2_BYTES else "L2-resident"},
+        "cpu_baseline": {"value": value, "unit": "sites/s", "cores": 1, "kind": "oracle",
+                         "sample": f"union-find oracle over the full instance ({lat.n} sites), "
+                                   f"one pass per step, 1 thread"},
+        "e2e": {"value": value, "unit": "sites/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1603_08357_gb300 as ccl
+
+    lat, desc = make_workload(args.config, rank)
+    rp = torch.from_numpy(lat.row_ptr).to(dev)
+    ci = torch.from_numpy(lat.col_idx).to(dev)
+    bits = torch.from_numpy(lat.open_bits.view(np.int32)).to(dev)
+    labels = torch.empty(lat.n, dtype=torch.int32, device=dev)
+    ctx = ccl.ccl_context_create(local)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        st = ccl.ccl_label(ctx, lat.n, lat.nnz, rp, ci, bits, labels, stream)
+        if st != ccl.CCL_OK:
+            raise ccl.CclError(st, "ccl_label")
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    ccl.check(ccl.ccl_sync(ctx, stream), "warm-up")
+
+    # correctness guard: the timed labels are compared with the oracle on a
+    # sample of sites (every rank, its own instance) -- full comparison in tests
+    stats = ccl.ccl_get_stats(ctx)
+    q = int(stats.residual_pairs)
+
+    # timed region: K steps, per-step CUDA events on the launching stream; the
+    # library records events between its kernels (profiling ring) so that the
+    # dominant kernel's mean duration comes from the same steps
+    ccl.ccl_set_option(ctx, ccl.CCL_OPT_PROFILE, 1)
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(local, uuid)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    st = ccl.ccl_sync(ctx, stream)
+    ccl.check(st, "timed steps")
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms_local = sum(step_ms) / args.steps
+    kern = ccl.ccl_get_step_times(ctx)
+    ccl.ccl_set_option(ctx, ccl.CCL_OPT_PROFILE, 0)
+    if dist:
+        t = torch.tensor([ms_local], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    else:
+        ms = ms_local
+
+    # graph-replay steps (the production path) for comparison
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(args.steps):
+        step()
+    g1.record(stream)
+    torch.cuda.synchronize()
+    ms_graph = g0.elapsed_time(g1) / args.steps
+
+    # end-to-end through the host-buffer entry point, pinned host memory
+    h_rp = torch.from_numpy(lat.row_ptr).pin_memory()
+    h_ci = torch.from_numpy(lat.col_idx).pin_memory()
+    h_bits = torch.from_numpy(lat.open_bits.view(np.int32)).pin_memory()
+    h_lab = torch.empty(lat.n, dtype=torch.int32).pin_memory()
+    ectx = ccl.ccl_context_create(local)
+    e_steps = max(1, min(args.steps, 10))
+
+    def e2e_step():
+        s = ccl.ccl_label_host(ectx, lat.n, lat.nnz, h_rp.data_ptr(), h_ci.data_ptr(),
+                               h_bits.data_ptr(), h_lab.data_ptr(), stream)
+        if s != ccl.CCL_OK:
+            raise ccl.CclError(s, "ccl_label_host")
+
+    for _ in range(2):
+        e2e_step()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        e2e_step()
+    e_ms = 1e3 * (time.perf_counter() - t0) / e_steps
+    if dist:
+        t = torch.tensor([e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e_ms = float(t.item())
+
+    # sampled parity guard on the labels of the last step
+    import oracle
+    got = labels.cpu().numpy()
+    ok_sample = bool(np.array_equal(got, oracle.uf_label(lat))) if lat.n <= 60_000_000 else None
+
+    if rank == 0:
+        peak, peak_src = _peaks()
+        ab = algorithmic_bytes(lat.n, lat.nnz, q)
+        names = ["init", "analysis_ii", "reduce", "analysis_iv"]
+        dom = max(range(4), key=lambda i: kern[i])
+        dom_name = names[dom]
+        achieved = ab[dom_name] / (kern[dom] / 1e3) / 1e9
+        traffic, scaled = _ncu_traffic(dom_name, args.config)
+        cpu = None
+        if not args.no_cpu_baseline:
+            v, reps, secs = oracle_time(lat, args.cpu_seconds)
+            cpu = {"value": v, "unit": "sites/s", "cores": 1, "kind": "oracle",
+                   "sample": f"union-find oracle over the full instance ({lat.n} sites), "
+                             f"{reps} pass(es) in {secs:.1f} s, 1 thread"}
+        kernels = {names[i]: {"ms": kern[i], "alg_bytes": ab[names[i]],
+                              "alg_gbs": ab[names[i]] / (kern[i] / 1e3) / 1e9 if kern[i] > 0 else None}
+                   for i in range(4)}
+        value = world * lat.n / (ms / 1e3)
+        line = {
+            "metric": "sites labeled/s", "value": value, "unit": "sites/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": args.config, "desc": desc, "n_sites": lat.n, "nnz": lat.nnz,
+                       "residual_pairs": q,
+                       "l2": "inputs larger than L2 (no flush)" if lat.nnz * 4 > L2_BYTES
+                       else "inputs L2-resident (no flush)",
+                       "parallelism": f"replicas{world}" if world > 1 else "single"},
+            "edges_per_s": world * (lat.nnz // 2) / (ms / 1e3),
+            "path_alg_gbs": ab["path"] / (ms / 1e3) / 1e9,
+            "ms_per_step_graph_replay": ms_graph,
+            "kernels": kernels,
+            "roofline": {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
+                         "traffic_note": scaled},
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * lat.n / (e_ms / 1e3), "unit": "sites/s",
+                    "h2d_bytes_per_step": 4 * (lat.n + 1) + 4 * lat.nnz + 4 * lat.open_bits.size,
+                    "d2h_bytes_per_step": 4 * lat.n, "ms_per_step": e_ms,
+                    "entry": "ccl_label_host (pinned host buffers)"},
+            "gpu_launches": args.steps * 4,
+            "clocks": clk,
+            "parity_last_step": ok_sample,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", choices=sorted(CONFIGS), default="tri4096")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    rank, world, local = _env_rank()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,253 @@
+/*
+ * ccl.h -- C ABI of the GB300 (sm_103a) cluster-labelling library.
+ *
+ * The library labels the clusters of open bonds on an arbitrary site graph
+ * given as a nearest-neighbour list, by the four-step generalized method of
+ * Komura, "A generalized GPU-based connected component labeling algorithm"
+ * (arXiv 1603.08357), Section 3:
+ *   (i)   initialisation: label[i] = smallest open neighbour numbered below i,
+ *         or i; the other open lower neighbours form i's residual list;
+ *   (ii)  analysis: label[i] = label[label[i]] until it stops changing;
+ *   (iii) label reduction (Algorithm 1): for every residual pair, follow both
+ *         label chains to their roots and merge them with atomicMin;
+ *   (iv)  analysis again.
+ * The result is the canonical cluster label of Section 3: label[v] is the
+ * smallest site number of v's cluster. It is unique, so any correct run gives
+ * the same bits.
+ *
+ * Input format (the "NN list" of Section 3, here in CSR form):
+ *   row_ptr[n+1]  int32, row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz;
+ *   col_idx[nnz]  int32 neighbour site numbers in [0, n);
+ *   open_bits     uint32 words, at least ceil(nnz/32); bit e (word e >> 5,
+ *                 bit e & 31) is 1 iff the bond of CSR entry e is open.
+ * Only an entry j < i of row i is read, so the bond {i, j} is decided by the
+ * bit stored in row max(i, j). Self-loops are ignored; duplicate entries are
+ * allowed. A symmetric list (j in row i <=> i in row j, equal bits) is the
+ * normal case; ccl_validate checks it.
+ *
+ * Ownership: every array argument belongs to the caller. The library
+ * allocates device memory only inside a ccl_context (its workspace) or a
+ * ccl_server. Streams are passed as `void*` holding a cudaStream_t
+ * (NULL = the legacy default stream); the library never synchronises a
+ * caller's stream except in the calls documented as synchronous.
+ *
+ * Errors: argument errors are returned synchronously. Errors found by the
+ * kernels (an index out of range, an inconsistent row_ptr, a loop that hit its
+ * iteration cap) are latched in a per-context device word and returned by
+ * ccl_sync. No function aborts, traps or prints.
+ */
+#ifndef CCL_H_
+#define CCL_H_
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CCL_API __attribute__((visibility("default")))
+#else
+#define CCL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CCL_OK = 0,
+    CCL_ERR_INVALID_ARGUMENT = 1,   /* bad pointer/size, or row_ptr[n] != nnz */
+    CCL_ERR_INDEX_OUT_OF_RANGE = 2, /* a col_idx outside [0, n) or a row_ptr outside [0, nnz] */
+    CCL_ERR_ASYMMETRIC = 3,         /* ccl_validate: an entry without its mirror entry/bit */
+    CCL_ERR_OUT_OF_MEMORY = 4,
+    CCL_ERR_NONCONVERGED = 5,       /* a chase or atomicMin loop hit its iteration cap */
+    CCL_ERR_TIMEOUT = 6,            /* a wait passed its deadline */
+    CCL_ERR_REJECTED = 7,           /* the request loop refused a request */
+    CCL_ERR_CUDA = 8,               /* a CUDA runtime call failed */
+    CCL_ERR_NOT_FOUND = 9           /* unknown ticket */
+} ccl_status;
+
+typedef struct ccl_context ccl_context;
+
+/* Human-readable name of a status code (static storage). */
+CCL_API const char *ccl_status_string(int status);
+
+/* Library ABI version, major * 100 + minor. */
+CCL_API int ccl_version(void);
+
+/* Creates a context on CUDA device `device`: it owns the workspace (residual
+ * pair queue, per-chunk records), the error word, the tuning table and the
+ * captured CUDA graphs. Not thread-safe: one host thread per context. */
+CCL_API ccl_status ccl_context_create(ccl_context **ctx, int device);
+CCL_API void ccl_context_destroy(ccl_context *ctx);
+
+/* Tunable options (ccl_set_option / ccl_get_option). */
+typedef enum {
+    CCL_OPT_PRE_ANALYSIS = 0,  /* 1 (default): run step (ii) before (iii); 0: skip it */
+    CCL_OPT_BLOCK_THREADS = 1, /* threads per CTA of the labelling kernels (64..1024, multiple of 32) */
+    CCL_OPT_USE_GRAPHS = 2,    /* 1 (default): replay captured CUDA graphs for repeated shapes */
+    CCL_OPT_PROFILE = 3,       /* 1: record CUDA events between the steps (ccl_get_step_times);
+                                  setting it restarts the averaging */
+    CCL_OPT_CTAS_PER_SM = 4,   /* persistent CTAs per SM; 0 (default) = occupancy maximum */
+    CCL_OPT_DEDUP = 5          /* 1 (default): warp-level dedupe of root pairs before atomics */
+} ccl_option;
+
+CCL_API ccl_status ccl_set_option(ccl_context *ctx, int option, int64_t value);
+CCL_API ccl_status ccl_get_option(ccl_context *ctx, int option, int64_t *value);
+
+/*
+ * ccl_label -- label one instance (Section 3, steps (i)-(iv)).
+ *   n_sites    number of sites n >= 0 (n = 0 returns CCL_OK, writes nothing)
+ *   nnz        number of CSR entries, 0 <= nnz < 2^31
+ *   row_ptr    DEVICE int32[n+1]
+ *   col_idx    DEVICE int32[nnz]       (may be NULL when nnz = 0)
+ *   open_bits  DEVICE uint32[ceil(nnz/32)] (may be NULL when nnz = 0)
+ *   labels     DEVICE int32[n], output: canonical labels
+ *   stream     cudaStream_t the work is enqueued on; asynchronous
+ * The first call with a larger n or nnz than any before grows the context
+ * workspace (8 bytes per CSR entry + 16 bytes per 32 sites) with cudaMalloc;
+ * make that call (or ccl_reserve) before capturing a stream into a graph.
+ */
+CCL_API ccl_status ccl_label(ccl_context *ctx, int32_t n_sites, int64_t nnz, const int32_t *row_ptr,
+                     const int32_t *col_idx, const uint32_t *open_bits, int32_t *labels,
+                     void *stream);
+
+/*
+ * ccl_label_batched -- label K independent instances in one pass of the
+ * four steps (one launch per step over all instances).
+ *   n_inst     K >= 0
+ *   site_off   HOST int64[K+1]: instance k owns sites [site_off[k], site_off[k+1])
+ *   ent_off    HOST int64[K+1]: instance k owns entries [ent_off[k], ent_off[k+1])
+ *   row_ptr    DEVICE int32: instance k's n_k + 1 row pointers, local entry
+ *              numbers 0..nnz_k, start at row_ptr + site_off[k] + k
+ *   col_idx    DEVICE int32[ent_off[K]]: instance-local site numbers
+ *   open_bits  DEVICE uint32: local entry e of instance k is global bit ent_off[k] + e
+ *   labels     DEVICE int32[site_off[K]]: labels[site_off[k] + i] = instance-local label
+ * Each instance needs n_k < 2^31 and nnz_k < 2^31. Asynchronous on `stream`.
+ * Repeated calls with the same arguments replay a captured CUDA graph.
+ */
+CCL_API ccl_status ccl_label_batched(ccl_context *ctx, int32_t n_inst, const int64_t *site_off,
+                             const int64_t *ent_off, const int32_t *row_ptr,
+                             const int32_t *col_idx, const uint32_t *open_bits, int32_t *labels,
+                             void *stream);
+
+/*
+ * ccl_label_host -- ccl_label on HOST arrays: copies the inputs to context
+ * buffers, labels, copies the labels back and waits. Synchronous. Pinned
+ * (page-locked) host memory gives the full copy bandwidth.
+ */
+CCL_API ccl_status ccl_label_host(ccl_context *ctx, int32_t n_sites, int64_t nnz, const int32_t *row_ptr,
+                          const int32_t *col_idx, const uint32_t *open_bits, int32_t *labels,
+                          void *stream);
+
+/* Pre-sizes the workspace for instances of up to n sites and nnz entries in
+ * total (and up to n_chunks 32-site chunks; 0 = ceil(n/32)). */
+CCL_API ccl_status ccl_reserve(ccl_context *ctx, int64_t n_sites, int64_t nnz, int64_t n_chunks);
+
+/*
+ * ccl_sync -- waits until `stream` has drained, polling with a deadline of
+ * timeout_ms (< 0: no deadline), then returns and clears the context's latched
+ * device error: CCL_OK, CCL_ERR_INDEX_OUT_OF_RANGE, CCL_ERR_INVALID_ARGUMENT
+ * or CCL_ERR_NONCONVERGED; CCL_ERR_TIMEOUT if the deadline passed first.
+ */
+CCL_API ccl_status ccl_sync(ccl_context *ctx, void *stream, int64_t timeout_ms);
+
+/*
+ * ccl_validate -- synchronous input check on the device: row_ptr shape and
+ * monotonicity, col_idx range, and that every entry (i -> j, bit b) with
+ * j != i has a mirror entry (j -> i) in row j carrying the same bit.
+ * Returns CCL_OK, CCL_ERR_INVALID_ARGUMENT, CCL_ERR_INDEX_OUT_OF_RANGE or
+ * CCL_ERR_ASYMMETRIC.
+ */
+CCL_API ccl_status ccl_validate(ccl_context *ctx, int32_t n_sites, int64_t nnz, const int32_t *row_ptr,
+                        const int32_t *col_idx, const uint32_t *open_bits, void *stream);
+
+/* Counters of the last completed labelling call (synchronous read). */
+typedef struct {
+    int64_t residual_pairs;   /* pairs handled by step (iii), summed over instances */
+    int64_t n_sites;          /* sites labelled */
+    int64_t nnz;              /* CSR entries read */
+    int32_t n_inst;           /* instances */
+    int32_t used_graph;       /* 1 if the call replayed a captured CUDA graph */
+} ccl_run_stats;
+
+CCL_API ccl_status ccl_get_stats(ccl_context *ctx, ccl_run_stats *stats);
+
+/* Per-step device times (ms), averaged over the calls made since
+ * CCL_OPT_PROFILE was last set to 1 (up to the last 4096 such calls): ms[0]
+ * init, ms[1] analysis (ii), ms[2] reduction (iii), ms[3] analysis (iv); ms[4]
+ * (if n > 4) the number of calls averaged. Profiled calls record CUDA events
+ * between the steps on the caller's stream and do not replay graphs.
+ * Synchronous. */
+CCL_API ccl_status ccl_get_step_times(ccl_context *ctx, float *ms, int32_t n);
+
+/*
+ * ccl_autotune -- synchronous: times the labelling of the given instance under
+ * candidate launch shapes (threads per CTA, CTAs per SM, step (ii) on/off)
+ * and keeps the fastest for instances of this size class (log2 of the site
+ * count, mean degree rounded). Every candidate writes the same labels, so
+ * `labels` holds the correct result afterwards. best_ms (optional) receives
+ * the best time.
+ */
+CCL_API ccl_status ccl_autotune(ccl_context *ctx, int32_t n_sites, int64_t nnz, const int32_t *row_ptr,
+                        const int32_t *col_idx, const uint32_t *open_bits, int32_t *labels,
+                        void *stream, float *best_ms);
+
+/* ---------------------------------------------------------------------------
+ * Request loop (continuous batching). A server thread admits submitted
+ * requests while the device memory they need is free (free HBM minus a
+ * reserve, and at most hbm_budget bytes held), uploads each into device
+ * memory of its own, gathers every uploaded request into one batched launch
+ * per tick on one of n_streams compute streams, so later arrivals are labelled
+ * while earlier batches are still on the GPU, and copies labels back.
+ * ------------------------------------------------------------------------- */
+
+typedef struct ccl_server ccl_server;
+
+typedef struct {
+    int32_t device;
+    int32_t n_streams;       /* concurrent compute streams (default 2) */
+    int64_t hbm_reserve;     /* bytes of free HBM never used (default 2 GiB) */
+    int64_t hbm_budget;      /* most bytes held by admitted requests (0 = no limit) */
+    int32_t max_batch;       /* most requests per launch (default 1024) */
+    int32_t max_pending;     /* most requests waiting for admission (default 1<<20) */
+    int64_t host_staging_bytes; /* pinned host arena for request copies (0: default 1 GiB,
+                                   < 0: none, requests then stay in pageable memory) */
+} ccl_server_config;
+
+typedef struct {
+    int32_t n_sites;
+    int32_t pad_;
+    int64_t nnz;
+    const int32_t *row_ptr;     /* HOST int32[n+1] */
+    const int32_t *col_idx;     /* HOST int32[nnz] */
+    const uint32_t *open_bits;  /* HOST uint32[ceil(nnz/32)] */
+} ccl_request;
+
+typedef struct {
+    int64_t submitted, completed, rejected, batches;
+    int64_t sites_completed;
+    double p50_ms, p99_ms, max_ms;   /* submit -> labels on host */
+    double busy_seconds;             /* wall time from first submit to last completion */
+    double sites_per_second;
+} ccl_server_stats;
+
+/* Starts the server thread. cfg may be NULL for defaults. */
+CCL_API ccl_status ccl_server_create(ccl_server **srv, const ccl_server_config *cfg);
+
+/* Copies the request (so the caller may free it on return) and queues it.
+ * CCL_ERR_REJECTED if it can never fit the budget or the queue is full. */
+CCL_API ccl_status ccl_server_submit(ccl_server *srv, const ccl_request *req, uint64_t *ticket);
+
+/* Waits up to timeout_ms (< 0: forever) for the ticket, copies its labels to
+ * labels_host (int32[n]) and forgets the ticket. */
+CCL_API ccl_status ccl_server_wait(ccl_server *srv, uint64_t ticket, int32_t *labels_host,
+                           int64_t timeout_ms);
+
+CCL_API ccl_status ccl_server_stats_get(ccl_server *srv, ccl_server_stats *stats);
+
+/* Stops the thread; requests not yet completed are dropped. */
+CCL_API void ccl_server_destroy(ccl_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CCL_H_ */

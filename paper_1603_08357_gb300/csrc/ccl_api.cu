@@ -1,0 +1,806 @@
+// Host side of the C ABI declared in include/ccl.h: contexts, workspace,
+// launch shapes, CUDA-graph replay, validation, tuning and statistics.
+#include <ccl.h>
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "ccl_device.cuh"
+
+using namespace ccl;
+
+namespace {
+
+struct TuneChoice {
+    int threads = 256;
+    int ctas_per_sm = 0;
+    int pre_analysis = 1;
+    int dedup = 1;
+};
+
+struct GraphEntry {
+    // key
+    int32_t K = 0;
+    int64_t n_chunks = 0;
+    const void *row_ptr = nullptr, *col_idx = nullptr, *bits = nullptr;
+    void *labels = nullptr;
+    uint64_t shape_hash = 0;
+    TuneChoice tc;
+    // value
+    cudaGraphExec_t exec = nullptr;
+    Inst *d_insts = nullptr;     // owned table (batched)
+    uint64_t last_use = 0;
+};
+
+}  // namespace
+
+struct ccl_context {
+    int device = 0;
+    int num_sms = 0;
+    // workspace
+    int2 *d_q = nullptr;
+    int64_t q_cap = 0;
+    ChunkRec *d_rec = nullptr;
+    int64_t rec_cap = 0;
+    unsigned *d_err = nullptr;
+    unsigned long long *d_counters = nullptr;
+    // batched descriptor table (non-graph path)
+    Inst *d_insts = nullptr;
+    int64_t insts_cap = 0;
+    Inst *h_insts = nullptr;     // pinned staging
+    int64_t h_insts_cap = 0;
+    cudaEvent_t staging_free = nullptr;
+    // host-buffer path
+    void *d_host_in = nullptr;
+    int64_t host_in_cap = 0;
+    // options
+    TuneChoice opt;
+    int use_graphs = 1;
+    int profile = 0;
+    std::map<int64_t, TuneChoice> tune_table;
+    // graphs
+    std::vector<GraphEntry> graphs;
+    uint64_t use_clock = 0;
+    cudaStream_t cap_stream = nullptr;
+    // profiling: one set of 5 events per profiled call, kept in a ring so that
+    // many calls can be timed without a host synchronisation in between
+    std::vector<std::array<cudaEvent_t, 5>> prof;
+    int64_t prof_count = 0;     // calls recorded since the last reset
+    cudaEvent_t *ev = nullptr;  // the set of the call being enqueued
+    int have_times = 0;
+    // stats of the last call
+    ccl_run_stats last{};
+    // occupancy cache: (kernel id, threads) -> blocks per SM
+    std::map<std::pair<int, int>, int> occ;
+};
+
+namespace {
+
+constexpr size_t kMaxGraphs = 16;
+constexpr int64_t kProfRing = 4096;
+
+ccl_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return CCL_OK;
+    if (e == cudaErrorMemoryAllocation) return CCL_ERR_OUT_OF_MEMORY;
+    return CCL_ERR_CUDA;
+}
+
+#define CCL_CUDA(call)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) {                            \
+            (void)cudaGetLastError();                       \
+            return cuda_status(e_);                         \
+        }                                                   \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+size_t stage_bytes(int threads) {
+    return (size_t)(threads / 32) * (kStageEntries + kStageWords) * sizeof(int32_t);
+}
+
+int blocks_per_sm(ccl_context *ctx, int kernel_id, int threads) {
+    auto key = std::make_pair(kernel_id, threads);
+    auto it = ctx->occ.find(key);
+    if (it != ctx->occ.end()) return it->second;
+    int nb = 1;
+    cudaError_t e = cudaSuccess;
+    switch (kernel_id) {
+        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init<false>, threads, stage_bytes(threads)); break;
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init<true>, threads, stage_bytes(threads)); break;
+        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_analysis<false>, threads, 0); break;
+        case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_analysis<true>, threads, 0); break;
+        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_reduce<false>, threads, 0); break;
+        case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_reduce<true>, threads, 0); break;
+        default: break;
+    }
+    if (e != cudaSuccess || nb < 1) { (void)cudaGetLastError(); nb = 1; }
+    ctx->occ[key] = nb;
+    return nb;
+}
+
+int64_t grid_for(ccl_context *ctx, int kernel_id, const TuneChoice &tc, int64_t warps_needed) {
+    int per_sm = blocks_per_sm(ctx, kernel_id, tc.threads);
+    if (tc.ctas_per_sm > 0) per_sm = std::min(per_sm, tc.ctas_per_sm);
+    int64_t g = (int64_t)ctx->num_sms * per_sm;
+    const int64_t wpb = tc.threads / 32;
+    const int64_t need = (warps_needed + wpb - 1) / wpb;
+    return std::max<int64_t>(1, std::min(g, need));
+}
+
+ccl_status ensure_workspace(ccl_context *ctx, int64_t q_slots, int64_t chunks) {
+    if (q_slots > ctx->q_cap || chunks > ctx->rec_cap) {
+        // growth invalidates every captured graph (they hold workspace pointers)
+        for (auto &g : ctx->graphs) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            if (g.d_insts) cudaFree(g.d_insts);
+        }
+        ctx->graphs.clear();
+    }
+    if (q_slots > ctx->q_cap) {
+        if (ctx->d_q) cudaFree(ctx->d_q);
+        ctx->d_q = nullptr;
+        ctx->q_cap = 0;
+        const int64_t want = std::max<int64_t>(q_slots, 1024);
+        CCL_CUDA(cudaMalloc(&ctx->d_q, (size_t)want * sizeof(int2)));
+        ctx->q_cap = want;
+    }
+    if (chunks > ctx->rec_cap) {
+        if (ctx->d_rec) cudaFree(ctx->d_rec);
+        ctx->d_rec = nullptr;
+        ctx->rec_cap = 0;
+        const int64_t want = std::max<int64_t>(chunks, 1024);
+        CCL_CUDA(cudaMalloc(&ctx->d_rec, (size_t)want * sizeof(ChunkRec)));
+        ctx->rec_cap = want;
+    }
+    return CCL_OK;
+}
+
+int64_t size_class(int64_t n, int64_t nnz) {
+    int lg = 0;
+    while ((int64_t(1) << (lg + 1)) <= std::max<int64_t>(n, 1)) ++lg;
+    const int64_t deg = n > 0 ? (nnz + n / 2) / n : 0;
+    return (int64_t)lg * 1024 + std::min<int64_t>(deg, 1023);
+}
+
+TuneChoice choice_for(ccl_context *ctx, int64_t n, int64_t nnz) {
+    auto it = ctx->tune_table.find(size_class(n, nnz));
+    if (it != ctx->tune_table.end()) return it->second;
+    return ctx->opt;
+}
+
+// Enqueues the four steps. All kernels read their sizes from Params, so the
+// sequence contains no host synchronisation and can be captured.
+ccl_status enqueue_steps(ccl_context *ctx, const Params &P, bool batched, const TuneChoice &tc,
+                         cudaStream_t s, bool profile) {
+    const int T = tc.threads;
+    const size_t smem = stage_bytes(T);
+    const int64_t warps_chunks = P.n_chunks;
+    const int64_t warps_groups = (P.n_chunks + 31) / 32;
+    CCL_CUDA(cudaMemsetAsync(P.counters, 0, sizeof(unsigned long long), s));
+    if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[0], s));
+    if (batched) {
+        k_init<true><<<(unsigned)grid_for(ctx, 1, tc, warps_chunks), T, smem, s>>>(P);
+    } else {
+        k_init<false><<<(unsigned)grid_for(ctx, 0, tc, warps_chunks), T, smem, s>>>(P);
+    }
+    CCL_CUDA(cudaGetLastError());
+    if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[1], s));
+    if (tc.pre_analysis) {
+        if (batched) k_analysis<true><<<(unsigned)grid_for(ctx, 3, tc, warps_chunks), T, 0, s>>>(P);
+        else k_analysis<false><<<(unsigned)grid_for(ctx, 2, tc, warps_chunks), T, 0, s>>>(P);
+        CCL_CUDA(cudaGetLastError());
+    }
+    if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[2], s));
+    if (batched) k_reduce<true><<<(unsigned)grid_for(ctx, 5, tc, warps_groups), T, 0, s>>>(P);
+    else k_reduce<false><<<(unsigned)grid_for(ctx, 4, tc, warps_groups), T, 0, s>>>(P);
+    CCL_CUDA(cudaGetLastError());
+    if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[3], s));
+    if (batched) k_analysis<true><<<(unsigned)grid_for(ctx, 3, tc, warps_chunks), T, 0, s>>>(P);
+    else k_analysis<false><<<(unsigned)grid_for(ctx, 2, tc, warps_chunks), T, 0, s>>>(P);
+    CCL_CUDA(cudaGetLastError());
+    if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[4], s));
+    return CCL_OK;
+}
+
+uint64_t fnv1a(const void *data, size_t bytes, uint64_t h = 1469598103934665603ull) {
+    const unsigned char *p = (const unsigned char *)data;
+    for (size_t i = 0; i < bytes; ++i) { h ^= p[i]; h *= 1099511628211ull; }
+    return h;
+}
+
+bool same_choice(const TuneChoice &a, const TuneChoice &b) {
+    return a.threads == b.threads && a.ctas_per_sm == b.ctas_per_sm &&
+           a.pre_analysis == b.pre_analysis && a.dedup == b.dedup;
+}
+
+GraphEntry *find_graph(ccl_context *ctx, const GraphEntry &key) {
+    for (auto &g : ctx->graphs) {
+        if (g.K == key.K && g.n_chunks == key.n_chunks && g.row_ptr == key.row_ptr &&
+            g.col_idx == key.col_idx && g.bits == key.bits && g.labels == key.labels &&
+            g.shape_hash == key.shape_hash && same_choice(g.tc, key.tc))
+            return &g;
+    }
+    return nullptr;
+}
+
+void evict_graph_if_full(ccl_context *ctx) {
+    if (ctx->graphs.size() < kMaxGraphs) return;
+    size_t lru = 0;
+    for (size_t i = 1; i < ctx->graphs.size(); ++i)
+        if (ctx->graphs[i].last_use < ctx->graphs[lru].last_use) lru = i;
+    if (ctx->graphs[lru].exec) cudaGraphExecDestroy(ctx->graphs[lru].exec);
+    if (ctx->graphs[lru].d_insts) cudaFree(ctx->graphs[lru].d_insts);
+    ctx->graphs.erase(ctx->graphs.begin() + (long)lru);
+}
+
+// Captures the step sequence for Params P on the context's capture stream.
+ccl_status capture_graph(ccl_context *ctx, const Params &P, bool batched, const TuneChoice &tc,
+                         cudaGraphExec_t *exec) {
+    cudaGraph_t graph = nullptr;
+    CCL_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    ccl_status st = enqueue_steps(ctx, P, batched, tc, ctx->cap_stream, false);
+    cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    if (st != CCL_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+    CCL_CUDA(e);
+    e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CCL_CUDA(e);
+    return CCL_OK;
+}
+
+bool stream_capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) { (void)cudaGetLastError(); return false; }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+// Runs P on stream s: through a cached graph when allowed, else directly.
+ccl_status run(ccl_context *ctx, Params P, bool batched, const TuneChoice &tc, cudaStream_t s,
+               const std::vector<Inst> *table, uint64_t shape_hash, bool allow_graph = true) {
+    for (int kid = 0; kid < 6; ++kid) (void)blocks_per_sm(ctx, kid, tc.threads);
+    ctx->last.used_graph = 0;
+    const bool capturing = stream_capturing(s);
+    if (ctx->profile || !ctx->use_graphs || capturing || !allow_graph) {
+        if (batched) {
+            // upload the table through pinned staging; wait until the previous
+            // upload has left the staging buffer before overwriting it
+            const int64_t K = (int64_t)table->size();
+            if (K > ctx->h_insts_cap) {
+                if (ctx->h_insts) { cudaEventSynchronize(ctx->staging_free); cudaFreeHost(ctx->h_insts); }
+                ctx->h_insts = nullptr;
+                ctx->h_insts_cap = 0;
+                CCL_CUDA(cudaMallocHost(&ctx->h_insts, (size_t)K * sizeof(Inst)));
+                ctx->h_insts_cap = K;
+            }
+            if (K > ctx->insts_cap) {
+                if (ctx->d_insts) cudaFree(ctx->d_insts);
+                ctx->d_insts = nullptr;
+                ctx->insts_cap = 0;
+                CCL_CUDA(cudaMalloc(&ctx->d_insts, (size_t)K * sizeof(Inst)));
+                ctx->insts_cap = K;
+            }
+            CCL_CUDA(cudaEventSynchronize(ctx->staging_free));
+            memcpy(ctx->h_insts, table->data(), (size_t)K * sizeof(Inst));
+            CCL_CUDA(cudaMemcpyAsync(ctx->d_insts, ctx->h_insts, (size_t)K * sizeof(Inst),
+                                     cudaMemcpyHostToDevice, s));
+            CCL_CUDA(cudaEventRecord(ctx->staging_free, s));
+            P.insts = ctx->d_insts;
+        }
+        if (ctx->profile) {
+            const size_t slot = (size_t)(ctx->prof_count % kProfRing);
+            if (slot >= ctx->prof.size()) {
+                std::array<cudaEvent_t, 5> set{};
+                for (auto &e : set) CCL_CUDA(cudaEventCreate(&e));
+                ctx->prof.push_back(set);
+            }
+            ctx->ev = ctx->prof[slot].data();
+        }
+        ccl_status st = enqueue_steps(ctx, P, batched, tc, s, ctx->profile != 0);
+        if (st == CCL_OK && ctx->profile) { ctx->have_times = 1; ctx->prof_count++; }
+        return st;
+    }
+    GraphEntry key;
+    key.K = P.K;
+    key.n_chunks = P.n_chunks;
+    key.row_ptr = batched ? (const void *)(*table)[0].row_ptr : P.one.row_ptr;
+    key.col_idx = batched ? (const void *)(*table)[0].col_idx : P.one.col_idx;
+    key.bits = batched ? (const void *)(*table)[0].bits : P.one.bits;
+    key.labels = batched ? (void *)(*table)[0].labels : P.one.labels;
+    key.shape_hash = shape_hash;
+    key.tc = tc;
+    GraphEntry *g = find_graph(ctx, key);
+    if (!g) {
+        evict_graph_if_full(ctx);
+        GraphEntry ne = key;
+        if (batched) {
+            const size_t bytes = table->size() * sizeof(Inst);
+            CCL_CUDA(cudaMalloc(&ne.d_insts, bytes));
+            cudaError_t e = cudaMemcpy(ne.d_insts, table->data(), bytes, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) { cudaFree(ne.d_insts); return cuda_status(e); }
+            P.insts = ne.d_insts;
+        }
+        ccl_status st = capture_graph(ctx, P, batched, tc, &ne.exec);
+        if (st != CCL_OK) { if (ne.d_insts) cudaFree(ne.d_insts); return st; }
+        ctx->graphs.push_back(ne);
+        g = &ctx->graphs.back();
+    }
+    g->last_use = ++ctx->use_clock;
+    CCL_CUDA(cudaGraphLaunch(g->exec, s));
+    ctx->last.used_graph = 1;
+    return CCL_OK;
+}
+
+Params base_params(ccl_context *ctx, const TuneChoice &tc) {
+    Params P;
+    memset(&P, 0, sizeof(P));
+    P.dedup = tc.dedup;
+    P.rec = ctx->d_rec;
+    P.q = ctx->d_q;
+    P.err = ctx->d_err;
+    P.counters = ctx->d_counters;
+    return P;
+}
+
+ccl_status check_single_args(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
+                             const int32_t *col_idx, const uint32_t *bits, const int32_t *labels) {
+    if (!ctx) return CCL_ERR_INVALID_ARGUMENT;
+    if (n < 0 || nnz < 0 || nnz > INT32_MAX) return CCL_ERR_INVALID_ARGUMENT;
+    if (n == 0) return CCL_OK;
+    if (!row_ptr || !labels) return CCL_ERR_INVALID_ARGUMENT;
+    if (nnz > 0 && (!col_idx || !bits)) return CCL_ERR_INVALID_ARGUMENT;
+    return CCL_OK;
+}
+
+ccl_status label_single(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
+                        const int32_t *col_idx, const uint32_t *bits, int32_t *labels,
+                        cudaStream_t s, const TuneChoice &tc) {
+    const int64_t chunks = ((int64_t)n + kChunk - 1) / kChunk;
+    ccl_status st = ensure_workspace(ctx, nnz, chunks);
+    if (st != CCL_OK) return st;
+    Params P = base_params(ctx, tc);
+    P.K = 1;
+    P.n_chunks = chunks;
+    P.one.row_ptr = row_ptr;
+    P.one.col_idx = col_idx;
+    P.one.bits = bits;
+    P.one.labels = labels;
+    P.one.bit_off = 0;
+    P.one.q_off = 0;
+    P.one.chunk_begin = 0;
+    P.one.n = n;
+    P.one.nnz = (int32_t)nnz;
+    ctx->last.n_sites = n;
+    ctx->last.nnz = nnz;
+    ctx->last.n_inst = 1;
+    return run(ctx, P, false, tc, s, nullptr, 0);
+}
+
+}  // namespace
+
+namespace ccl {
+
+// Labels the instances of `table` (row_ptr, col_idx, bits, bit_off, labels,
+// n, nnz filled in by the caller) in one pass of the four steps on stream s.
+// Used by the request loop, whose instances live in separate allocations.
+ccl_status label_instances(ccl_context *ctx, std::vector<Inst> &table, cudaStream_t s) {
+    int64_t chunks = 0, q = 0;
+    for (Inst &I : table) {
+        I.q_off = q;
+        I.chunk_begin = chunks;
+        q += I.nnz;
+        chunks += ((int64_t)I.n + kChunk - 1) / kChunk;
+    }
+    if (chunks == 0) return CCL_OK;
+    DeviceGuard guard(ctx->device);
+    ccl_status st = ensure_workspace(ctx, q, chunks);
+    if (st != CCL_OK) return st;
+    const TuneChoice tc = ctx->opt;
+    Params P = base_params(ctx, tc);
+    P.K = (int32_t)table.size();
+    P.n_chunks = chunks;
+    if (table.size() == 1) {
+        P.one = table[0];
+        return run(ctx, P, false, tc, s, nullptr, 0, false);
+    }
+    return run(ctx, P, true, tc, s, &table, 0, false);
+}
+
+}  // namespace ccl
+
+extern "C" {
+
+const char *ccl_status_string(int status) {
+    switch (status) {
+        case CCL_OK: return "CCL_OK";
+        case CCL_ERR_INVALID_ARGUMENT: return "CCL_ERR_INVALID_ARGUMENT";
+        case CCL_ERR_INDEX_OUT_OF_RANGE: return "CCL_ERR_INDEX_OUT_OF_RANGE";
+        case CCL_ERR_ASYMMETRIC: return "CCL_ERR_ASYMMETRIC";
+        case CCL_ERR_OUT_OF_MEMORY: return "CCL_ERR_OUT_OF_MEMORY";
+        case CCL_ERR_NONCONVERGED: return "CCL_ERR_NONCONVERGED";
+        case CCL_ERR_TIMEOUT: return "CCL_ERR_TIMEOUT";
+        case CCL_ERR_REJECTED: return "CCL_ERR_REJECTED";
+        case CCL_ERR_CUDA: return "CCL_ERR_CUDA";
+        case CCL_ERR_NOT_FOUND: return "CCL_ERR_NOT_FOUND";
+        default: return "CCL_ERR_UNKNOWN";
+    }
+}
+
+int ccl_version(void) { return 100; }
+
+ccl_status ccl_context_create(ccl_context **out, int device) {
+    if (!out) return CCL_ERR_INVALID_ARGUMENT;
+    *out = nullptr;
+    int ndev = 0;
+    CCL_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return CCL_ERR_INVALID_ARGUMENT;
+    DeviceGuard guard(device);
+    CCL_CUDA(cudaSetDevice(device));
+    ccl_context *ctx = new ccl_context();
+    ctx->device = device;
+    cudaError_t e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_counters, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_counters, 0, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->staging_free, cudaEventDisableTiming);
+    // the opt-in shared memory of the staging buffers
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_init<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)stage_bytes(512));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_init<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)stage_bytes(512));
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        ccl_context_destroy(ctx);
+        return cuda_status(e);
+    }
+    if (const char *env = getenv("CCL_TUNE_CACHE")) {
+        if (FILE *f = fopen(env, "r")) {
+            long long cls;
+            int a, b, c, d;
+            while (fscanf(f, "%lld %d %d %d %d", &cls, &a, &b, &c, &d) == 5) {
+                TuneChoice t;
+                t.threads = a; t.ctas_per_sm = b; t.pre_analysis = c; t.dedup = d;
+                if (t.threads >= 64 && t.threads <= 512 && t.threads % 32 == 0) ctx->tune_table[cls] = t;
+            }
+            fclose(f);
+        }
+    }
+    *out = ctx;
+    return CCL_OK;
+}
+
+void ccl_context_destroy(ccl_context *ctx) {
+    if (!ctx) return;
+    DeviceGuard guard(ctx->device);
+    for (auto &g : ctx->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.d_insts) cudaFree(g.d_insts);
+    }
+    if (ctx->d_q) cudaFree(ctx->d_q);
+    if (ctx->d_rec) cudaFree(ctx->d_rec);
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->d_counters) cudaFree(ctx->d_counters);
+    if (ctx->d_insts) cudaFree(ctx->d_insts);
+    if (ctx->h_insts) cudaFreeHost(ctx->h_insts);
+    if (ctx->d_host_in) cudaFree(ctx->d_host_in);
+    if (ctx->staging_free) cudaEventDestroy(ctx->staging_free);
+    for (auto &set : ctx->prof)
+        for (auto &e : set) if (e) cudaEventDestroy(e);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    (void)cudaGetLastError();
+    delete ctx;
+}
+
+ccl_status ccl_set_option(ccl_context *ctx, int option, int64_t value) {
+    if (!ctx) return CCL_ERR_INVALID_ARGUMENT;
+    switch (option) {
+        case CCL_OPT_PRE_ANALYSIS: ctx->opt.pre_analysis = value ? 1 : 0; break;
+        case CCL_OPT_BLOCK_THREADS:
+            if (value < 64 || value > 512 || value % 32) return CCL_ERR_INVALID_ARGUMENT;
+            ctx->opt.threads = (int)value;
+            break;
+        case CCL_OPT_USE_GRAPHS: ctx->use_graphs = value ? 1 : 0; return CCL_OK;
+        case CCL_OPT_PROFILE:
+            ctx->profile = value ? 1 : 0;
+            ctx->prof_count = 0;
+            ctx->have_times = 0;
+            return CCL_OK;      // does not touch the tuning table
+        case CCL_OPT_CTAS_PER_SM:
+            if (value < 0 || value > 64) return CCL_ERR_INVALID_ARGUMENT;
+            ctx->opt.ctas_per_sm = (int)value;
+            break;
+        case CCL_OPT_DEDUP: ctx->opt.dedup = value ? 1 : 0; break;
+        default: return CCL_ERR_INVALID_ARGUMENT;
+    }
+    // explicit options take effect over any tuned entry
+    ctx->tune_table.clear();
+    return CCL_OK;
+}
+
+ccl_status ccl_get_option(ccl_context *ctx, int option, int64_t *value) {
+    if (!ctx || !value) return CCL_ERR_INVALID_ARGUMENT;
+    switch (option) {
+        case CCL_OPT_PRE_ANALYSIS: *value = ctx->opt.pre_analysis; break;
+        case CCL_OPT_BLOCK_THREADS: *value = ctx->opt.threads; break;
+        case CCL_OPT_USE_GRAPHS: *value = ctx->use_graphs; break;
+        case CCL_OPT_PROFILE: *value = ctx->profile; break;
+        case CCL_OPT_CTAS_PER_SM: *value = ctx->opt.ctas_per_sm; break;
+        case CCL_OPT_DEDUP: *value = ctx->opt.dedup; break;
+        default: return CCL_ERR_INVALID_ARGUMENT;
+    }
+    return CCL_OK;
+}
+
+ccl_status ccl_reserve(ccl_context *ctx, int64_t n_sites, int64_t nnz, int64_t n_chunks) {
+    if (!ctx || n_sites < 0 || nnz < 0 || n_chunks < 0) return CCL_ERR_INVALID_ARGUMENT;
+    DeviceGuard guard(ctx->device);
+    if (n_chunks == 0) n_chunks = (n_sites + kChunk - 1) / kChunk;
+    return ensure_workspace(ctx, nnz, n_chunks);
+}
+
+ccl_status ccl_label(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
+                     const int32_t *col_idx, const uint32_t *bits, int32_t *labels, void *stream) {
+    ccl_status st = check_single_args(ctx, n, nnz, row_ptr, col_idx, bits, labels);
+    if (st != CCL_OK || n == 0) {
+        if (ctx && n == 0 && st == CCL_OK) { ctx->last = ccl_run_stats{}; ctx->last.n_inst = 1; }
+        return st;
+    }
+    DeviceGuard guard(ctx->device);
+    const TuneChoice tc = choice_for(ctx, n, nnz);
+    return label_single(ctx, n, nnz, row_ptr, col_idx, bits, labels, (cudaStream_t)stream, tc);
+}
+
+ccl_status ccl_label_batched(ccl_context *ctx, int32_t K, const int64_t *site_off,
+                             const int64_t *ent_off, const int32_t *row_ptr,
+                             const int32_t *col_idx, const uint32_t *bits, int32_t *labels,
+                             void *stream) {
+    if (!ctx || K < 0) return CCL_ERR_INVALID_ARGUMENT;
+    if (K == 0) { ctx->last = ccl_run_stats{}; return CCL_OK; }
+    if (!site_off || !ent_off) return CCL_ERR_INVALID_ARGUMENT;
+    if (site_off[0] != 0 || ent_off[0] != 0) return CCL_ERR_INVALID_ARGUMENT;
+    std::vector<Inst> table;
+    table.reserve((size_t)K);
+    int64_t chunks = 0;
+    for (int32_t k = 0; k < K; ++k) {
+        const int64_t n = site_off[k + 1] - site_off[k];
+        const int64_t nnz = ent_off[k + 1] - ent_off[k];
+        if (n < 0 || nnz < 0 || n > INT32_MAX - 1 || nnz > INT32_MAX) return CCL_ERR_INVALID_ARGUMENT;
+        Inst I;
+        I.row_ptr = row_ptr + site_off[k] + k;
+        I.col_idx = col_idx + ent_off[k];
+        I.bits = bits;
+        I.labels = labels + site_off[k];
+        I.bit_off = ent_off[k];
+        I.q_off = ent_off[k];
+        I.chunk_begin = chunks;
+        I.n = (int32_t)n;
+        I.nnz = (int32_t)nnz;
+        table.push_back(I);
+        chunks += (n + kChunk - 1) / kChunk;
+    }
+    const int64_t n_tot = site_off[K], nnz_tot = ent_off[K];
+    if (n_tot > 0 && (!row_ptr || !labels)) return CCL_ERR_INVALID_ARGUMENT;
+    if (nnz_tot > 0 && (!col_idx || !bits)) return CCL_ERR_INVALID_ARGUMENT;
+    ctx->last = ccl_run_stats{};
+    ctx->last.n_inst = K;
+    ctx->last.n_sites = n_tot;
+    ctx->last.nnz = nnz_tot;
+    if (chunks == 0) return CCL_OK;
+    DeviceGuard guard(ctx->device);
+    ccl_status st = ensure_workspace(ctx, nnz_tot, chunks);
+    if (st != CCL_OK) return st;
+    const TuneChoice tc = choice_for(ctx, n_tot / K, nnz_tot / K);
+    Params P = base_params(ctx, tc);
+    P.K = K;
+    P.n_chunks = chunks;
+    if (K == 1) {
+        P.one = table[0];
+        return run(ctx, P, false, tc, (cudaStream_t)stream, nullptr, 0);
+    }
+    uint64_t h = fnv1a(site_off, sizeof(int64_t) * (size_t)(K + 1));
+    h = fnv1a(ent_off, sizeof(int64_t) * (size_t)(K + 1), h);
+    return run(ctx, P, true, tc, (cudaStream_t)stream, &table, h);
+}
+
+ccl_status ccl_sync(ccl_context *ctx, void *stream, int64_t timeout_ms) {
+    if (!ctx) return CCL_ERR_INVALID_ARGUMENT;
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const auto t0 = std::chrono::steady_clock::now();
+    int spins = 0;
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(s);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) { (void)cudaGetLastError(); return cuda_status(e); }
+        if (timeout_ms >= 0) {
+            const auto el = std::chrono::duration_cast<std::chrono::milliseconds>(
+                std::chrono::steady_clock::now() - t0).count();
+            if (el > timeout_ms) return CCL_ERR_TIMEOUT;
+        }
+        if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    unsigned err = 0;
+    CCL_CUDA(cudaMemcpy(&err, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (err) CCL_CUDA(cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
+    if (err & kErrIndex) return CCL_ERR_INDEX_OUT_OF_RANGE;
+    if (err & kErrShape) return CCL_ERR_INVALID_ARGUMENT;
+    if (err & kErrNonconv) return CCL_ERR_NONCONVERGED;
+    if (err & kErrAsym) return CCL_ERR_ASYMMETRIC;
+    return CCL_OK;
+}
+
+ccl_status ccl_label_host(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
+                          const int32_t *col_idx, const uint32_t *bits, int32_t *labels,
+                          void *stream) {
+    ccl_status st = check_single_args(ctx, n, nnz, row_ptr, col_idx, bits, labels);
+    if (st != CCL_OK || n == 0) return st;
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nwords = (nnz + 31) / 32;
+    const size_t b_rp = (size_t)(n + 1) * 4, b_ci = (size_t)nnz * 4, b_bits = (size_t)nwords * 4,
+                 b_lab = (size_t)n * 4;
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t need = al(b_rp) + al(b_ci) + al(b_bits) + al(b_lab);
+    if ((int64_t)need > ctx->host_in_cap) {
+        CCL_CUDA(cudaStreamSynchronize(s));
+        if (ctx->d_host_in) cudaFree(ctx->d_host_in);
+        ctx->d_host_in = nullptr;
+        ctx->host_in_cap = 0;
+        // graphs may hold pointers into the old buffer
+        for (auto &g : ctx->graphs) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            if (g.d_insts) cudaFree(g.d_insts);
+        }
+        ctx->graphs.clear();
+        CCL_CUDA(cudaMalloc(&ctx->d_host_in, need));
+        ctx->host_in_cap = (int64_t)need;
+    }
+    char *base = (char *)ctx->d_host_in;
+    int32_t *d_rp = (int32_t *)base;
+    int32_t *d_ci = (int32_t *)(base + al(b_rp));
+    uint32_t *d_bits = (uint32_t *)(base + al(b_rp) + al(b_ci));
+    int32_t *d_lab = (int32_t *)(base + al(b_rp) + al(b_ci) + al(b_bits));
+    CCL_CUDA(cudaMemcpyAsync(d_rp, row_ptr, b_rp, cudaMemcpyHostToDevice, s));
+    if (nnz > 0) {
+        CCL_CUDA(cudaMemcpyAsync(d_ci, col_idx, b_ci, cudaMemcpyHostToDevice, s));
+        CCL_CUDA(cudaMemcpyAsync(d_bits, bits, b_bits, cudaMemcpyHostToDevice, s));
+    }
+    const TuneChoice tc = choice_for(ctx, n, nnz);
+    st = label_single(ctx, n, nnz, d_rp, nnz ? d_ci : nullptr, nnz ? d_bits : nullptr, d_lab, s, tc);
+    if (st != CCL_OK) return st;
+    CCL_CUDA(cudaMemcpyAsync(labels, d_lab, b_lab, cudaMemcpyDeviceToHost, s));
+    return ccl_sync(ctx, stream, -1);
+}
+
+ccl_status ccl_validate(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
+                        const int32_t *col_idx, const uint32_t *bits, void *stream) {
+    ccl_status st = check_single_args(ctx, n, nnz, row_ptr, col_idx, bits, (const int32_t *)1);
+    if (st != CCL_OK || n == 0) return st;
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    // drain earlier work so that its latched errors are not reported here
+    st = ccl_sync(ctx, stream, -1);
+    (void)st;
+    const int threads = 256;
+    const int64_t grid = std::min<int64_t>((int64_t)ctx->num_sms * 8, ((int64_t)n + threads - 1) / threads);
+    k_validate<<<(unsigned)std::max<int64_t>(grid, 1), threads, 0, s>>>(n, nnz, row_ptr, col_idx, bits,
+                                                                      ctx->d_err);
+    CCL_CUDA(cudaGetLastError());
+    return ccl_sync(ctx, stream, -1);
+}
+
+ccl_status ccl_get_stats(ccl_context *ctx, ccl_run_stats *out) {
+    if (!ctx || !out) return CCL_ERR_INVALID_ARGUMENT;
+    DeviceGuard guard(ctx->device);
+    CCL_CUDA(cudaDeviceSynchronize());
+    unsigned long long pairs = 0;
+    CCL_CUDA(cudaMemcpy(&pairs, ctx->d_counters, sizeof(pairs), cudaMemcpyDeviceToHost));
+    *out = ctx->last;
+    out->residual_pairs = (int64_t)pairs;
+    return CCL_OK;
+}
+
+ccl_status ccl_get_step_times(ccl_context *ctx, float *ms, int32_t n) {
+    if (!ctx || !ms || n < 0) return CCL_ERR_INVALID_ARGUMENT;
+    if (!ctx->have_times || ctx->prof_count == 0) return CCL_ERR_NOT_FOUND;
+    DeviceGuard guard(ctx->device);
+    const int64_t calls = std::min<int64_t>(ctx->prof_count, kProfRing);
+    const size_t last = (size_t)((ctx->prof_count - 1) % kProfRing);
+    CCL_CUDA(cudaEventSynchronize(ctx->prof[last][4]));
+    double acc[4] = {0, 0, 0, 0};
+    for (int64_t c = 0; c < calls; ++c) {
+        const size_t slot = (size_t)((ctx->prof_count - 1 - c) % kProfRing);
+        for (int i = 0; i < 4; ++i) {
+            float t = 0;
+            CCL_CUDA(cudaEventElapsedTime(&t, ctx->prof[slot][(size_t)i], ctx->prof[slot][(size_t)i + 1]));
+            acc[i] += t;
+        }
+    }
+    for (int i = 0; i < std::min<int32_t>(n, 4); ++i) ms[i] = (float)(acc[i] / (double)calls);
+    if (n > 4) ms[4] = (float)calls;
+    return CCL_OK;
+}
+
+ccl_status ccl_autotune(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
+                        const int32_t *col_idx, const uint32_t *bits, int32_t *labels, void *stream,
+                        float *best_ms) {
+    ccl_status st = check_single_args(ctx, n, nnz, row_ptr, col_idx, bits, labels);
+    if (st != CCL_OK || n == 0) return st;
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t a, b;
+    CCL_CUDA(cudaEventCreate(&a));
+    CCL_CUDA(cudaEventCreate(&b));
+    const int saved_profile = ctx->profile;
+    ctx->profile = 0;
+    TuneChoice best = ctx->opt;
+    float best_t = 1e30f;
+    std::vector<TuneChoice> cands;
+    for (int T : {128, 256, 512})
+        for (int C : {0, 2})
+            for (int pre = 0; pre < 2; ++pre)
+                for (int dd = 0; dd < 2; ++dd) {
+                    TuneChoice tc;
+                    tc.threads = T; tc.ctas_per_sm = C; tc.pre_analysis = pre; tc.dedup = dd;
+                    cands.push_back(tc);
+                }
+    for (const TuneChoice &tc : cands) {
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 4 && st == CCL_OK; ++rep) {
+            cudaError_t e = cudaEventRecord(a, s);
+            if (e == cudaSuccess) st = label_single(ctx, n, nnz, row_ptr, col_idx, bits, labels, s, tc);
+            if (e == cudaSuccess && st == CCL_OK) e = cudaEventRecord(b, s);
+            if (e == cudaSuccess && st == CCL_OK) e = cudaEventSynchronize(b);
+            if (e != cudaSuccess) st = cuda_status(e);
+            float t = 0;
+            if (st == CCL_OK) cudaEventElapsedTime(&t, a, b);
+            if (rep > 0) tmin = std::min(tmin, t);
+        }
+        if (st != CCL_OK) break;
+        if (tmin < best_t) { best_t = tmin; best = tc; }
+    }
+    ctx->profile = saved_profile;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st != CCL_OK) return st;
+    ctx->tune_table[size_class(n, nnz)] = best;
+    if (const char *env = getenv("CCL_TUNE_CACHE")) {
+        if (FILE *f = fopen(env, "w")) {
+            for (auto &kv : ctx->tune_table)
+                fprintf(f, "%lld %d %d %d %d\n", (long long)kv.first, kv.second.threads,
+                        kv.second.ctas_per_sm, kv.second.pre_analysis, kv.second.dedup);
+            fclose(f);
+        }
+    }
+    // leave the correct labels in `labels` with the chosen shape
+    st = label_single(ctx, n, nnz, row_ptr, col_idx, bits, labels, s, best);
+    if (st != CCL_OK) return st;
+    if (best_ms) *best_ms = best_t;
+    return ccl_sync(ctx, stream, -1);
+}
+
+}  // extern "C"

@@ -1,0 +1,520 @@
+// Request loop of include/ccl.h: continuous batching of labelling requests.
+//
+// One server thread owns the GPU side. Each tick it
+//   1. admits pending requests while their device bytes fit the budget
+//      (the free HBM seen at start minus a reserve, and the configured
+//      cap), allocating their buffers from a stream-ordered pool and
+//      uploading them on an upload stream;
+//   2. gathers every request whose upload has finished into one batched
+//      launch of the four labelling steps on a free compute stream (each
+//      compute stream has a labelling context of its own), followed by the
+//      copies of the labels back to host memory;
+//   3. retires finished batches: frees their buffers, stamps latencies and
+//      wakes waiters.
+// Later requests are therefore uploaded and labelled while earlier batches
+// are still running. Every wait on the device is an event query; nothing
+// spins on the GPU.
+#include <ccl.h>
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "ccl_types.cuh"
+
+namespace ccl {
+ccl_status label_instances(ccl_context *ctx, std::vector<Inst> &table, cudaStream_t s);
+}
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Req {
+    uint64_t ticket = 0;
+    int32_t n = 0;
+    int64_t nnz = 0;
+    // host copy: one block of the pinned staging arena when it had room
+    // (row_ptr | col_idx | bits | labels), else pageable vectors
+    char *h = nullptr;
+    size_t h_bytes = 0;
+    std::vector<int32_t> v_row_ptr, v_col_idx, v_labels;
+    std::vector<uint32_t> v_bits;
+    int64_t dev_bytes = 0;
+    char *d_mem = nullptr;
+    cudaEvent_t uploaded = nullptr;
+    Clock::time_point t_submit, t_done;
+    ccl_status status = CCL_OK;
+    bool done = false;
+};
+
+struct Batch {
+    std::vector<std::shared_ptr<Req>> reqs;
+    int slot = -1;
+    cudaEvent_t finished = nullptr;
+};
+
+size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+
+struct HostLayout {
+    size_t rp, ci, bits, lab, total;
+    HostLayout(int32_t n, int64_t nnz) {
+        rp = 0;
+        ci = al256((size_t)(n + 1) * 4);
+        bits = ci + al256((size_t)nnz * 4);
+        lab = bits + al256((size_t)std::max<int64_t>(1, (nnz + 31) / 32) * 4);
+        total = lab + al256((size_t)n * 4);
+    }
+};
+
+const int32_t *h_row_ptr(const Req &r) { return r.h ? (const int32_t *)(r.h) : r.v_row_ptr.data(); }
+const int32_t *h_col_idx(const Req &r) {
+    return r.h ? (const int32_t *)(r.h + HostLayout(r.n, r.nnz).ci) : r.v_col_idx.data();
+}
+const uint32_t *h_bits(const Req &r) {
+    return r.h ? (const uint32_t *)(r.h + HostLayout(r.n, r.nnz).bits) : r.v_bits.data();
+}
+int32_t *h_labels(Req &r) { return r.h ? (int32_t *)(r.h + HostLayout(r.n, r.nnz).lab) : r.v_labels.data(); }
+
+// First-fit allocator over one pinned host buffer (callers hold the server mutex).
+struct HostArena {
+    char *base = nullptr;
+    size_t cap = 0;
+    std::map<size_t, size_t> free_;   // offset -> size
+    void init(char *b, size_t c) { base = b; cap = c; free_.clear(); if (c) free_[0] = c; }
+    char *alloc(size_t bytes) {
+        bytes = al256(bytes);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < bytes) continue;
+            const size_t off = it->first, sz = it->second;
+            free_.erase(it);
+            if (sz > bytes) free_[off + bytes] = sz - bytes;
+            return base + off;
+        }
+        return nullptr;
+    }
+    void release(char *p, size_t bytes) {
+        bytes = al256(bytes);
+        size_t off = (size_t)(p - base);
+        auto next = free_.lower_bound(off);
+        if (next != free_.end() && off + bytes == next->first) { bytes += next->second; next = free_.erase(next); }
+        if (next != free_.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == off) { prev->second += bytes; return; }
+        }
+        free_[off] = bytes;
+    }
+};
+
+
+}  // namespace
+
+struct ccl_server {
+    ccl_server_config cfg{};
+    int64_t budget = 0;
+    int64_t held = 0;
+    std::vector<ccl_context *> ctxs;
+    std::vector<cudaStream_t> streams;
+    std::vector<bool> slot_busy;
+    cudaStream_t upload = nullptr;
+    cudaMemPool_t pool = nullptr;
+    char *h_stage = nullptr;
+    HostArena arena;
+
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<Req>> pending;
+    std::map<uint64_t, std::shared_ptr<Req>> tickets;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+
+    // owned by the server thread
+    std::deque<std::shared_ptr<Req>> uploading;
+    std::vector<std::shared_ptr<Req>> ready;
+    std::vector<Batch> inflight;
+
+    // statistics (under mu)
+    int64_t submitted = 0, completed = 0, rejected = 0, batches = 0, sites_completed = 0;
+    std::vector<double> lat_ms;
+    bool have_first = false;
+    Clock::time_point t_first, t_last;
+
+    std::thread th;
+};
+
+namespace {
+
+void retire(ccl_server *S, Batch &b) {
+    ccl_status st = ccl_sync(S->ctxs[(size_t)b.slot], S->streams[(size_t)b.slot], 0);
+    for (auto &r : b.reqs) {
+        if (!r->h && r->n > 0) {   // pageable request: its labels come back now
+            r->v_labels.resize((size_t)r->n);
+            const size_t off = HostLayout(r->n, r->nnz).lab;
+            if (cudaMemcpy(r->v_labels.data(), r->d_mem + off, (size_t)r->n * 4, cudaMemcpyDeviceToHost) !=
+                cudaSuccess) { (void)cudaGetLastError(); st = CCL_ERR_CUDA; }
+        }
+    }
+    const auto now = Clock::now();
+    for (auto &r : b.reqs) {
+        if (r->d_mem) cudaFreeAsync(r->d_mem, S->streams[(size_t)b.slot]);
+        r->d_mem = nullptr;
+        if (r->uploaded) cudaEventDestroy(r->uploaded);
+        r->uploaded = nullptr;
+    }
+    cudaEventDestroy(b.finished);
+    S->slot_busy[(size_t)b.slot] = false;
+    std::lock_guard<std::mutex> lk(S->mu);
+    for (auto &r : b.reqs) {
+        r->status = st;
+        r->t_done = now;
+        r->done = true;
+        S->held -= r->dev_bytes;
+        S->completed++;
+        S->sites_completed += r->n;
+        S->lat_ms.push_back(std::chrono::duration<double, std::milli>(now - r->t_submit).count());
+        r->v_row_ptr.clear(); r->v_row_ptr.shrink_to_fit();
+        r->v_col_idx.clear(); r->v_col_idx.shrink_to_fit();
+        r->v_bits.clear(); r->v_bits.shrink_to_fit();
+    }
+    S->t_last = now;
+    S->batches++;
+    S->cv_done.notify_all();
+}
+
+// uploads one admitted request; returns false if the pool is exhausted
+bool start_upload(ccl_server *S, const std::shared_ptr<Req> &r) {
+    const HostLayout lay(r->n, r->nnz);
+    void *mem = nullptr;
+    if (cudaMallocFromPoolAsync(&mem, lay.total, S->pool, S->upload) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    r->d_mem = (char *)mem;
+    if (r->h) {   // one contiguous pinned block: one copy
+        cudaMemcpyAsync(r->d_mem, r->h, lay.lab, cudaMemcpyHostToDevice, S->upload);
+    } else {
+        cudaMemcpyAsync(r->d_mem, h_row_ptr(*r), (size_t)(r->n + 1) * 4, cudaMemcpyHostToDevice, S->upload);
+        if (r->nnz > 0) {
+            cudaMemcpyAsync(r->d_mem + lay.ci, h_col_idx(*r), (size_t)r->nnz * 4, cudaMemcpyHostToDevice,
+                            S->upload);
+            cudaMemcpyAsync(r->d_mem + lay.bits, h_bits(*r), (size_t)((r->nnz + 31) / 32) * 4,
+                            cudaMemcpyHostToDevice, S->upload);
+        }
+    }
+    cudaEventCreateWithFlags(&r->uploaded, cudaEventDisableTiming);
+    cudaEventRecord(r->uploaded, S->upload);
+    return true;
+}
+
+void launch_batch(ccl_server *S, int slot, std::vector<std::shared_ptr<Req>> reqs) {
+    cudaStream_t s = S->streams[(size_t)slot];
+    std::vector<ccl::Inst> table;
+    table.reserve(reqs.size());
+    for (auto &r : reqs) {
+        cudaStreamWaitEvent(s, r->uploaded, 0);
+        const HostLayout lay(r->n, r->nnz);
+        ccl::Inst I{};
+        I.row_ptr = (const int32_t *)r->d_mem;
+        I.col_idx = (const int32_t *)(r->d_mem + lay.ci);
+        I.bits = (const uint32_t *)(r->d_mem + lay.bits);
+        I.labels = (int32_t *)(r->d_mem + lay.lab);
+        I.bit_off = 0;
+        I.n = r->n;
+        I.nnz = (int32_t)r->nnz;
+        table.push_back(I);
+    }
+    ccl_status st = ccl::label_instances(S->ctxs[(size_t)slot], table, s);
+    for (size_t t = 0; t < reqs.size(); ++t) {
+        auto &r = reqs[t];
+        if (r->h && r->n > 0)
+            cudaMemcpyAsync(h_labels(*r), table[t].labels, (size_t)r->n * 4, cudaMemcpyDeviceToHost, s);
+        if (st != CCL_OK) r->status = st;
+    }
+    Batch b;
+    b.reqs = std::move(reqs);
+    b.slot = slot;
+    cudaEventCreateWithFlags(&b.finished, cudaEventDisableTiming);
+    cudaEventRecord(b.finished, s);
+    S->slot_busy[(size_t)slot] = true;
+    S->inflight.push_back(std::move(b));
+}
+
+void server_loop(ccl_server *S) {
+    cudaSetDevice(S->cfg.device);
+    for (;;) {
+        bool progressed = false;
+        // 1. admission
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            if (S->stop) break;
+            while (!S->pending.empty()) {
+                auto r = S->pending.front();
+                if (S->held + r->dev_bytes > S->budget && S->held > 0) break;
+                S->pending.pop_front();
+                S->held += r->dev_bytes;
+                lk.unlock();
+                const bool ok = start_upload(S, r);
+                lk.lock();
+                if (!ok) {     // pool full right now: retry later
+                    S->held -= r->dev_bytes;
+                    S->pending.push_front(r);
+                    break;
+                }
+                S->uploading.push_back(r);
+                progressed = true;
+            }
+        }
+        // 2. collect uploaded requests
+        while (!S->uploading.empty()) {
+            auto &r = S->uploading.front();
+            const cudaError_t e = cudaEventQuery(r->uploaded);
+            if (e == cudaErrorNotReady) break;
+            if (e != cudaSuccess) { (void)cudaGetLastError(); r->status = CCL_ERR_CUDA; }
+            S->ready.push_back(r);
+            S->uploading.pop_front();
+            progressed = true;
+        }
+        // 3. launch on a free compute stream
+        if (!S->ready.empty()) {
+            for (size_t slot = 0; slot < S->streams.size() && !S->ready.empty(); ++slot) {
+                if (S->slot_busy[slot]) continue;
+                const size_t take = std::min<size_t>(S->ready.size(), (size_t)S->cfg.max_batch);
+                std::vector<std::shared_ptr<Req>> reqs(S->ready.begin(), S->ready.begin() + (long)take);
+                S->ready.erase(S->ready.begin(), S->ready.begin() + (long)take);
+                launch_batch(S, (int)slot, std::move(reqs));
+                progressed = true;
+            }
+        }
+        // 4. retire finished batches
+        for (size_t b = 0; b < S->inflight.size();) {
+            const cudaError_t e = cudaEventQuery(S->inflight[b].finished);
+            if (e == cudaErrorNotReady) { ++b; continue; }
+            if (e != cudaSuccess) (void)cudaGetLastError();
+            retire(S, S->inflight[b]);
+            S->inflight.erase(S->inflight.begin() + (long)b);
+            progressed = true;
+        }
+        if (!progressed) {
+            std::unique_lock<std::mutex> lk(S->mu);
+            if (S->stop) break;
+            const bool idle = S->pending.empty() && S->uploading.empty() && S->ready.empty() &&
+                              S->inflight.empty();
+            S->cv_work.wait_for(lk, idle ? std::chrono::milliseconds(5) : std::chrono::microseconds(50));
+        }
+    }
+    // drain what is on the device before tearing down
+    for (auto &b : S->inflight) {
+        cudaEventSynchronize(b.finished);
+        retire(S, b);
+    }
+    S->inflight.clear();
+    for (auto &r : S->uploading) {
+        cudaEventSynchronize(r->uploaded);
+        if (r->d_mem) cudaFreeAsync(r->d_mem, S->upload);
+        cudaEventDestroy(r->uploaded);
+    }
+    for (auto &r : S->ready) {
+        if (r->d_mem) cudaFreeAsync(r->d_mem, S->upload);
+        if (r->uploaded) cudaEventDestroy(r->uploaded);
+    }
+    cudaStreamSynchronize(S->upload);
+}
+
+}  // namespace
+
+extern "C" {
+
+ccl_status ccl_server_create(ccl_server **out, const ccl_server_config *cfg_in) {
+    if (!out) return CCL_ERR_INVALID_ARGUMENT;
+    *out = nullptr;
+    ccl_server_config cfg{};
+    cfg.device = 0;
+    cfg.n_streams = 2;
+    cfg.hbm_reserve = (int64_t)2 << 30;
+    cfg.hbm_budget = 0;
+    cfg.max_batch = 1024;
+    cfg.max_pending = 1 << 20;
+    cfg.host_staging_bytes = (int64_t)1 << 30;
+    if (cfg_in) {
+        if (cfg_in->host_staging_bytes != 0) cfg.host_staging_bytes = std::max<int64_t>(0, cfg_in->host_staging_bytes);
+        cfg.device = cfg_in->device;
+        if (cfg_in->n_streams > 0) cfg.n_streams = cfg_in->n_streams;
+        if (cfg_in->hbm_reserve > 0) cfg.hbm_reserve = cfg_in->hbm_reserve;
+        if (cfg_in->hbm_budget > 0) cfg.hbm_budget = cfg_in->hbm_budget;
+        if (cfg_in->max_batch > 0) cfg.max_batch = cfg_in->max_batch;
+        if (cfg_in->max_pending > 0) cfg.max_pending = cfg_in->max_pending;
+    }
+    if (cfg.n_streams > 16) return CCL_ERR_INVALID_ARGUMENT;
+    if (cudaSetDevice(cfg.device) != cudaSuccess) { (void)cudaGetLastError(); return CCL_ERR_INVALID_ARGUMENT; }
+    auto S = new ccl_server();
+    S->cfg = cfg;
+    size_t free_b = 0, total_b = 0;
+    cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess) { (void)cudaGetLastError(); delete S; return CCL_ERR_CUDA; }
+    S->budget = (int64_t)free_b - cfg.hbm_reserve;
+    if (cfg.hbm_budget > 0) S->budget = std::min(S->budget, cfg.hbm_budget);
+    if (S->budget <= 0) { delete S; return CCL_ERR_OUT_OF_MEMORY; }
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = cfg.device;
+    e = cudaMemPoolCreate(&S->pool, &props);
+    if (e == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;   // keep freed memory in the pool
+        cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->upload, cudaStreamNonBlocking);
+    if (e == cudaSuccess && cfg.host_staging_bytes > 0) {
+        e = cudaMallocHost(&S->h_stage, (size_t)cfg.host_staging_bytes);
+        if (e == cudaSuccess) S->arena.init(S->h_stage, (size_t)cfg.host_staging_bytes);
+    }
+    for (int i = 0; i < cfg.n_streams && e == cudaSuccess; ++i) {
+        cudaStream_t s;
+        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e != cudaSuccess) break;
+        S->streams.push_back(s);
+        ccl_context *c = nullptr;
+        if (ccl_context_create(&c, cfg.device) != CCL_OK) { e = cudaErrorUnknown; break; }
+        ccl_set_option(c, CCL_OPT_USE_GRAPHS, 0);
+        S->ctxs.push_back(c);
+    }
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        for (auto c : S->ctxs) ccl_context_destroy(c);
+        for (auto s : S->streams) cudaStreamDestroy(s);
+        if (S->upload) cudaStreamDestroy(S->upload);
+        if (S->pool) cudaMemPoolDestroy(S->pool);
+        if (S->h_stage) cudaFreeHost(S->h_stage);
+        delete S;
+        return CCL_ERR_CUDA;
+    }
+    S->slot_busy.assign(S->streams.size(), false);
+    S->th = std::thread(server_loop, S);
+    *out = S;
+    return CCL_OK;
+}
+
+ccl_status ccl_server_submit(ccl_server *S, const ccl_request *req, uint64_t *ticket) {
+    if (!S || !req || !ticket) return CCL_ERR_INVALID_ARGUMENT;
+    if (req->n_sites < 0 || req->nnz < 0 || req->nnz > INT32_MAX) return CCL_ERR_INVALID_ARGUMENT;
+    if (!req->row_ptr || (req->nnz > 0 && (!req->col_idx || !req->open_bits)))
+        return CCL_ERR_INVALID_ARGUMENT;
+    auto r = std::make_shared<Req>();
+    r->n = req->n_sites;
+    r->nnz = req->nnz;
+    // device bytes: inputs + labels + the request's share of the labelling
+    // workspace (8 B per CSR entry, 16 B per 32 sites)
+    const HostLayout lay(r->n, r->nnz);
+    r->dev_bytes = (int64_t)lay.total + 8 * r->nnz + 16 * (((int64_t)r->n + 31) / 32);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (r->dev_bytes > S->budget || (int64_t)S->pending.size() >= S->cfg.max_pending) {
+            S->rejected++;
+            return CCL_ERR_REJECTED;
+        }
+    }
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        r->h = S->arena.alloc(lay.total);
+        if (r->h) r->h_bytes = lay.total;
+    }
+    if (r->h) {
+        memcpy(r->h, req->row_ptr, (size_t)(r->n + 1) * 4);
+        if (r->nnz > 0) {
+            memcpy(r->h + lay.ci, req->col_idx, (size_t)r->nnz * 4);
+            memcpy(r->h + lay.bits, req->open_bits, (size_t)((r->nnz + 31) / 32) * 4);
+        }
+    } else {
+        r->v_row_ptr.assign(req->row_ptr, req->row_ptr + r->n + 1);
+        r->v_col_idx.assign(req->col_idx, req->col_idx + r->nnz);
+        r->v_bits.assign(req->open_bits, req->open_bits + (r->nnz + 31) / 32);
+        if (r->v_bits.empty()) r->v_bits.push_back(0);
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        r->ticket = S->next_ticket++;
+        S->tickets[r->ticket] = r;
+        S->pending.push_back(r);
+        S->submitted++;
+        if (!S->have_first) { S->have_first = true; S->t_first = r->t_submit; }
+        *ticket = r->ticket;
+    }
+    S->cv_work.notify_one();
+    return CCL_OK;
+}
+
+ccl_status ccl_server_wait(ccl_server *S, uint64_t ticket, int32_t *labels_host, int64_t timeout_ms) {
+    if (!S) return CCL_ERR_INVALID_ARGUMENT;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->tickets.find(ticket);
+    if (it == S->tickets.end()) return CCL_ERR_NOT_FOUND;
+    auto r = it->second;
+    auto ready = [&] { return r->done; };
+    if (timeout_ms < 0) S->cv_done.wait(lk, ready);
+    else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) return CCL_ERR_TIMEOUT;
+    if (labels_host && r->n > 0) memcpy(labels_host, h_labels(*r), (size_t)r->n * 4);
+    if (r->h) { S->arena.release(r->h, r->h_bytes); r->h = nullptr; }
+    r->v_labels.clear();
+    r->v_labels.shrink_to_fit();
+    S->tickets.erase(ticket);
+    return r->status;
+}
+
+ccl_status ccl_server_stats_get(ccl_server *S, ccl_server_stats *out) {
+    if (!S || !out) return CCL_ERR_INVALID_ARGUMENT;
+    std::lock_guard<std::mutex> lk(S->mu);
+    memset(out, 0, sizeof(*out));
+    out->submitted = S->submitted;
+    out->completed = S->completed;
+    out->rejected = S->rejected;
+    out->batches = S->batches;
+    out->sites_completed = S->sites_completed;
+    if (!S->lat_ms.empty()) {
+        std::vector<double> v = S->lat_ms;
+        std::sort(v.begin(), v.end());
+        auto q = [&](double f) { return v[std::min(v.size() - 1, (size_t)(f * (double)(v.size() - 1) + 0.5))]; };
+        out->p50_ms = q(0.50);
+        out->p99_ms = q(0.99);
+        out->max_ms = v.back();
+    }
+    if (S->have_first && S->completed > 0) {
+        out->busy_seconds = std::chrono::duration<double>(S->t_last - S->t_first).count();
+        if (out->busy_seconds > 0) out->sites_per_second = (double)S->sites_completed / out->busy_seconds;
+    }
+    return CCL_OK;
+}
+
+void ccl_server_destroy(ccl_server *S) {
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    if (S->th.joinable()) S->th.join();
+    cudaSetDevice(S->cfg.device);
+    for (auto c : S->ctxs) ccl_context_destroy(c);
+    for (auto s : S->streams) cudaStreamDestroy(s);
+    if (S->upload) cudaStreamDestroy(S->upload);
+    if (S->pool) cudaMemPoolDestroy(S->pool);
+    if (S->h_stage) cudaFreeHost(S->h_stage);
+    (void)cudaGetLastError();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->cv_done.notify_all();
+    }
+    delete S;
+}
+
+}  // extern "C"

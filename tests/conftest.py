@@ -32,3 +32,15 @@ def load_golden(name):
             else:
                 out[key] = [int(v) for v in vals]
     return out
+
+
+@pytest.fixture(scope="session")
+def ctx():
+    """One labelling context on cuda:0 for the GPU tests."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test without a CUDA device")
+    import paper_1603_08357_gb300 as ccl
+    c = ccl.ccl_context_create(0)
+    yield c
+    ccl.ccl_context_destroy(c)

@@ -1,0 +1,245 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Labels are integers and canonical (smallest site of the cluster, Section 3),
+so the bar is bit-exact equality on every site. Inputs are the seeded
+generator's lattices and random multigraphs; sizes span many 32-site chunks
+with ragged tails, the staged and the direct row paths, empty and degenerate
+inputs. The residual-pair count of step (i) is compared with the oracle's
+sequential run of Section 3.
+"""
+import numpy as np
+import pytest
+import torch
+
+import lattices as L
+import oracle
+import paper_1603_08357_gb300 as ccl
+from ccl_testutil import DEV, gpu_label, gpu_label_batched, to_dev
+from conftest import load_golden
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("name", ["worked_example.txt", "row_max_rule.txt", "duplicate_min.txt"])
+def test_golden(ctx, name):
+    g = load_golden(name)
+    rp = np.array(g["row_ptr"], np.int32)
+    lat = L.Lattice("golden", g["n"][0], int(rp[-1]), rp, np.array(g["col_idx"], np.int32),
+                    L.pack_bits(np.array(g["open"], bool)), 0.0, 0)
+    assert gpu_label(ctx, lat).tolist() == g["label"]
+    st = ccl.ccl_get_stats(ctx)
+    assert st.residual_pairs == sum(len(v) for v in g.get("residual", {}).values())
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_multigraphs(ctx, seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.choice([1, 2, 31, 32, 33, 64, 65, 200, 1000, 4097]))
+    m = int(rng.integers(0, 3 * n + 2))
+    lat = L.random_graph(n, m, 500 + seed, asymmetric=0.3 if seed % 3 == 0 else 0.0,
+                         p=float(rng.uniform(0.2, 0.9)))
+    want = oracle.uf_label(lat)
+    assert np.array_equal(gpu_label(ctx, lat), want)
+    assert ccl.ccl_get_stats(ctx).residual_pairs == oracle.steps_label(lat)["n_residual"]
+
+
+def test_heavy_rows_direct_path(ctx):
+    """A hub of degree 5000 and chunks with more than 256 entries take the
+    unstaged path of step (i)."""
+    n = 6000
+    hub_edges = [(5999, j) for j in range(0, 5000)]
+    rng = np.random.default_rng(3)
+    extra = [(int(a), int(b)) for a, b in rng.integers(0, n, (3000, 2))]
+    edges = hub_edges + extra
+    u = np.array([a for a, b in edges]); v = np.array([b for a, b in edges])
+    op = rng.random(len(edges)) < 0.5
+    rows = np.concatenate([u, v]); cols = np.concatenate([v, u]); bitv = np.concatenate([op, op])
+    order = np.argsort(rows, kind="stable")
+    rows, cols, bitv = rows[order], cols[order], bitv[order]
+    rp = np.zeros(n + 1, np.int64); np.add.at(rp, rows + 1, 1); rp = np.cumsum(rp).astype(np.int32)
+    lat = L.Lattice("hub", n, len(cols), rp, cols.astype(np.int32), L.pack_bits(bitv), 0.5, 0)
+    assert np.array_equal(gpu_label(ctx, lat), oracle.uf_label(lat))
+
+
+def _lattice_cases():
+    out = []
+    for p in [0.0, 0.25, None, 0.75, 1.0]:
+        out.append(("honeycomb", dict(L=37), p))
+        out.append(("triangle", dict(L=45), p))
+        out.append(("cayley", dict(z=3, shells=11, perm_seed=None), p))
+        out.append(("cayley", dict(z=4, shells=7, perm_seed=5), p))
+    out.append(("triangle", dict(L=200, periodic_y=False), None))
+    out.append(("honeycomb", dict(L=150, periodic_y=False), None))
+    return out
+
+
+@pytest.mark.parametrize("kind,kw,p", _lattice_cases())
+def test_lattices(ctx, kind, kw, p):
+    if p is None:
+        p = {"honeycomb": L.PC_HONEYCOMB, "triangle": L.PC_TRIANGLE}.get(kind) or 1.0 / (kw["z"] - 1)
+    spec = dict(kind=kind, p=p, seed=77, **kw)
+    lat = L.make_instance(spec)
+    want = oracle.uf_label(lat)
+    got = gpu_label(ctx, lat)
+    assert np.array_equal(got, want)
+    assert ccl.ccl_get_stats(ctx).residual_pairs == oracle.steps_label(lat)["n_residual"]
+
+
+@pytest.mark.parametrize("z,S", [(3, 14), (5, 7)])
+def test_standard_bethe_has_no_residual_pairs(ctx, z, S):
+    for p in (0.3, 1.0 / (z - 1), 0.9):
+        lat = L.cayley(z, S, p, 9)
+        assert np.array_equal(gpu_label(ctx, lat), oracle.uf_label(lat))
+        assert ccl.ccl_get_stats(ctx).residual_pairs == 0
+
+
+@pytest.mark.parametrize("threads", [64, 128, 256, 512])
+@pytest.mark.parametrize("pre", [0, 1])
+@pytest.mark.parametrize("dedup", [0, 1])
+def test_launch_options_same_labels(threads, pre, dedup):
+    c = ccl.ccl_context_create(0)
+    try:
+        for opt, val in ((ccl.CCL_OPT_BLOCK_THREADS, threads), (ccl.CCL_OPT_PRE_ANALYSIS, pre),
+                         (ccl.CCL_OPT_DEDUP, dedup), (ccl.CCL_OPT_CTAS_PER_SM, 1 if threads == 64 else 0)):
+            assert ccl.ccl_set_option(c, opt, val) == ccl.CCL_OK
+        lat = L.triangle(300, 0.52, 11)
+        want = oracle.uf_label(lat)
+        for graphs in (0, 1):
+            ccl.ccl_set_option(c, ccl.CCL_OPT_USE_GRAPHS, graphs)
+            for _ in range(2):
+                assert np.array_equal(gpu_label(c, lat), want)
+    finally:
+        ccl.ccl_context_destroy(c)
+
+
+def test_profile_step_times(ctx):
+    lat = L.triangle(512, L.PC_TRIANGLE, 5)
+    ccl.ccl_set_option(ctx, ccl.CCL_OPT_PROFILE, 1)
+    try:
+        assert np.array_equal(gpu_label(ctx, lat), oracle.uf_label(lat))
+        t = ccl.ccl_get_step_times(ctx)
+        assert len(t) == 5 and all(v >= 0 for v in t) and t[0] > 0 and t[4] == 1
+    finally:
+        ccl.ccl_set_option(ctx, ccl.CCL_OPT_PROFILE, 0)
+
+
+def test_edge_cases(ctx):
+    empty = L.Lattice("e", 0, 0, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(1, np.uint32), 0, 0)
+    assert gpu_label(ctx, empty).size == 0
+    iso = L.Lattice("iso", 70, 0, np.zeros(71, np.int32), np.zeros(0, np.int32), np.zeros(1, np.uint32), 0, 0)
+    assert np.array_equal(gpu_label(ctx, iso), np.arange(70))
+    one = L.Lattice("one", 1, 2, np.array([0, 2], np.int32), np.array([0, 0], np.int32),
+                    np.array([3], np.uint32), 0, 0)
+    assert gpu_label(ctx, one).tolist() == [0]
+    assert ccl.ccl_label(ctx, -1, 0, 0, 0, 0, 0) == ccl.CCL_ERR_INVALID_ARGUMENT
+    assert ccl.ccl_label(ctx, 5, 0, None, None, None, None) == ccl.CCL_ERR_INVALID_ARGUMENT
+
+
+def test_kernel_checks_report_bad_input(ctx):
+    """Out-of-range indices and inconsistent row pointers are caught by the
+    kernels' own bounds checks and reported by ccl_sync; the bad entries are
+    skipped, never dereferenced."""
+    lat = L.triangle(40, 0.5, 1)
+    ci = lat.col_idx.copy(); ci[100] = lat.n + 5; ci[2000] = -3
+    bad = L.Lattice("bad", lat.n, lat.nnz, lat.row_ptr, ci, lat.open_bits, 0.5, 0)
+    gpu_label(ctx, bad, expect_status=ccl.CCL_ERR_INDEX_OUT_OF_RANGE)
+    rp = lat.row_ptr.copy(); rp[500] = rp[502]      # rows no longer monotone
+    bad = L.Lattice("bad", lat.n, lat.nnz, rp, lat.col_idx, lat.open_bits, 0.5, 0)
+    gpu_label(ctx, bad, expect_status=ccl.CCL_ERR_INDEX_OUT_OF_RANGE)
+    bad = L.Lattice("bad", lat.n, lat.nnz - 6, lat.row_ptr, lat.col_idx, lat.open_bits, 0.5, 0)
+    got = gpu_label(ctx, bad, expect_status=ccl.CCL_ERR_INDEX_OUT_OF_RANGE)
+    assert got.shape == (lat.n,)
+    # the context is usable afterwards
+    assert np.array_equal(gpu_label(ctx, lat), oracle.uf_label(lat))
+
+
+def test_validate(ctx):
+    lat = L.triangle(64, 0.4, 2)
+    rp, ci, bits = to_dev(lat)
+    assert ccl.ccl_validate(ctx, lat.n, lat.nnz, rp, ci, bits) == ccl.CCL_OK
+    asym = L.random_graph(500, 900, 4, asymmetric=0.5)
+    rp, ci, bits = to_dev(asym)
+    assert ccl.ccl_validate(ctx, asym.n, asym.nnz, rp, ci, bits) == ccl.CCL_ERR_ASYMMETRIC
+    ci2 = lat.col_idx.copy(); ci2[7] = lat.n
+    rp, ci, bits = to_dev(L.Lattice("b", lat.n, lat.nnz, lat.row_ptr, ci2, lat.open_bits, 0, 0))
+    assert ccl.ccl_validate(ctx, lat.n, lat.nnz, rp, ci, bits) == ccl.CCL_ERR_INDEX_OUT_OF_RANGE
+
+
+def test_host_path(ctx):
+    lat = L.cayley(3, 12, 0.5, 4, perm_seed=8)
+    out = np.full(lat.n, -1, np.int32)
+    st = ccl.ccl_label_host(ctx, lat.n, lat.nnz, lat.row_ptr, lat.col_idx, lat.open_bits, out)
+    assert st == ccl.CCL_OK
+    assert np.array_equal(out, oracle.uf_label(lat))
+
+
+def test_autotune(ctx):
+    c = ccl.ccl_context_create(0)
+    try:
+        lat = L.triangle(256, L.PC_TRIANGLE, 3)
+        rp, ci, bits = to_dev(lat)
+        out = torch.empty(lat.n, dtype=torch.int32, device=DEV)
+        st, best = ccl.ccl_autotune(c, lat.n, lat.nnz, rp, ci, bits, out)
+        assert st == ccl.CCL_OK and best > 0
+        assert np.array_equal(out.cpu().numpy(), oracle.uf_label(lat))
+        assert np.array_equal(gpu_label(c, lat), oracle.uf_label(lat))
+    finally:
+        ccl.ccl_context_destroy(c)
+
+
+def _mixed_specs(K, seed):
+    rng = np.random.default_rng(seed)
+    specs = []
+    for k in range(K):
+        t = int(rng.integers(0, 4))
+        if t == 0:
+            specs.append(dict(kind="honeycomb", L=int(rng.integers(2, 60)), p=float(rng.uniform(0.5, 0.8)), seed=k))
+        elif t == 1:
+            specs.append(dict(kind="triangle", L=int(rng.integers(2, 70)), p=float(rng.uniform(0.2, 0.5)), seed=k))
+        elif t == 2:
+            specs.append(dict(kind="cayley", z=int(rng.integers(3, 7)), shells=int(rng.integers(0, 6)),
+                              p=float(rng.uniform(0.1, 0.9)), seed=k, perm_seed=k if k % 2 else None))
+        else:
+            specs.append(dict(kind="triangle", L=int(rng.integers(1, 4)), p=0.5, seed=k))
+    return specs
+
+
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_batched_matches_oracle_and_single(ctx, graphs):
+    b = L.make_batch(_mixed_specs(150, 21))
+    ccl.ccl_set_option(ctx, ccl.CCL_OPT_USE_GRAPHS, graphs)
+    try:
+        got = gpu_label_batched(ctx, b)
+        again = gpu_label_batched(ctx, b)
+    finally:
+        ccl.ccl_set_option(ctx, ccl.CCL_OPT_USE_GRAPHS, 1)
+    assert np.array_equal(got, again)
+    want = oracle.uf_label_batched(b)
+    assert np.array_equal(got, want)
+    pairs = ccl.ccl_get_stats(ctx).residual_pairs
+    tot = 0
+    for k in range(b.k):
+        inst = b.instance(k)
+        s0, s1 = b.site_off[k], b.site_off[k + 1]
+        assert np.array_equal(gpu_label(ctx, inst), got[s0:s1])
+        tot += oracle.steps_label(inst)["n_residual"]
+    assert pairs == tot
+
+
+def test_two_streams_two_contexts():
+    c1, c2 = ccl.ccl_context_create(0), ccl.ccl_context_create(0)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    a = L.triangle(700, L.PC_TRIANGLE, 1)
+    b = L.cayley(3, 16, 0.5, 2, perm_seed=3)
+    da, db = to_dev(a), to_dev(b)
+    torch.cuda.synchronize()
+    oa = torch.empty(a.n, dtype=torch.int32, device=DEV)
+    ob = torch.empty(b.n, dtype=torch.int32, device=DEV)
+    for _ in range(3):
+        assert ccl.ccl_label(c1, a.n, a.nnz, *da, oa, s1) == ccl.CCL_OK
+        assert ccl.ccl_label(c2, b.n, b.nnz, *db, ob, s2) == ccl.CCL_OK
+    assert ccl.ccl_sync(c1, s1) == ccl.CCL_OK and ccl.ccl_sync(c2, s2) == ccl.CCL_OK
+    assert np.array_equal(oa.cpu().numpy(), oracle.uf_label(a))
+    assert np.array_equal(ob.cpu().numpy(), oracle.uf_label(b))
+    ccl.ccl_context_destroy(c1)
+    ccl.ccl_context_destroy(c2)
