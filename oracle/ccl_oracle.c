@@ -93,7 +93,7 @@ int oracle_uf_label(int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_
 int oracle_bfs_label(int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
                      const uint32_t *bits, int64_t bit_off, int32_t *label) {
     if (check_csr(n, nnz, row_ptr, col_idx)) return -1;
-    if (n == 0) return 0;
+    if (n <= 0) return 0;
     /* adjacency of the open bond set, both directions */
     int64_t *deg = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
     if (!deg) return -2;
@@ -104,9 +104,10 @@ int oracle_bfs_label(int32_t n, int64_t nnz, const int32_t *row_ptr, const int32
             if (j < i && bit_at(bits, bit_off + e)) { deg[i + 1]++; deg[j + 1]++; nb++; }
         }
     for (int32_t v = 0; v < n; ++v) deg[v + 1] += deg[v];
+    const size_t un = (size_t)(uint32_t)n;
     int32_t *adj = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * nb + 1));
-    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
-    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * un);
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * un);
     if (!adj || !fill || !queue) { free(deg); free(adj); free(fill); free(queue); return -2; }
     for (int32_t v = 0; v < n; ++v) fill[v] = deg[v];
     for (int32_t i = 0; i < n; ++i)

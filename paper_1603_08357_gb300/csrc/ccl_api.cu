@@ -35,6 +35,8 @@ struct GraphEntry {
     const void *row_ptr = nullptr, *col_idx = nullptr, *bits = nullptr;
     void *labels = nullptr;
     uint64_t shape_hash = 0;
+    Inst one{};                      // the instance (single path), compared exactly
+    std::vector<int64_t> offsets;    // site_off and ent_off (batched), compared exactly
     TuneChoice tc;
     // value
     cudaGraphExec_t exec = nullptr;
@@ -238,7 +240,8 @@ GraphEntry *find_graph(ccl_context *ctx, const GraphEntry &key) {
     for (auto &g : ctx->graphs) {
         if (g.K == key.K && g.n_chunks == key.n_chunks && g.row_ptr == key.row_ptr &&
             g.col_idx == key.col_idx && g.bits == key.bits && g.labels == key.labels &&
-            g.shape_hash == key.shape_hash && same_choice(g.tc, key.tc))
+            g.shape_hash == key.shape_hash && same_choice(g.tc, key.tc) &&
+            memcmp(&g.one, &key.one, sizeof(Inst)) == 0 && g.offsets == key.offsets)
             return &g;
     }
     return nullptr;
@@ -277,7 +280,8 @@ bool stream_capturing(cudaStream_t s) {
 
 // Runs P on stream s: through a cached graph when allowed, else directly.
 ccl_status run(ccl_context *ctx, Params P, bool batched, const TuneChoice &tc, cudaStream_t s,
-               const std::vector<Inst> *table, uint64_t shape_hash, bool allow_graph = true) {
+               const std::vector<Inst> *table, uint64_t shape_hash, bool allow_graph = true,
+               const std::vector<int64_t> *offsets = nullptr) {
     for (int kid = 0; kid < 6; ++kid) (void)blocks_per_sm(ctx, kid, tc.threads);
     ctx->last.used_graph = 0;
     const bool capturing = stream_capturing(s);
@@ -329,6 +333,8 @@ ccl_status run(ccl_context *ctx, Params P, bool batched, const TuneChoice &tc, c
     key.labels = batched ? (void *)(*table)[0].labels : P.one.labels;
     key.shape_hash = shape_hash;
     key.tc = tc;
+    if (!batched) key.one = P.one;
+    if (offsets) key.offsets = *offsets;
     GraphEntry *g = find_graph(ctx, key);
     if (!g) {
         evict_graph_if_full(ctx);
@@ -393,7 +399,8 @@ ccl_status label_single(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t 
     ctx->last.n_sites = n;
     ctx->last.nnz = nnz;
     ctx->last.n_inst = 1;
-    return run(ctx, P, false, tc, s, nullptr, 0);
+    // the graph key covers every field of the instance (sizes included)
+    return run(ctx, P, false, tc, s, nullptr, fnv1a(&P.one, sizeof(Inst)));
 }
 
 }  // namespace
@@ -619,11 +626,13 @@ ccl_status ccl_label_batched(ccl_context *ctx, int32_t K, const int64_t *site_of
     P.n_chunks = chunks;
     if (K == 1) {
         P.one = table[0];
-        return run(ctx, P, false, tc, (cudaStream_t)stream, nullptr, 0);
+        return run(ctx, P, false, tc, (cudaStream_t)stream, nullptr, fnv1a(&P.one, sizeof(Inst)));
     }
     uint64_t h = fnv1a(site_off, sizeof(int64_t) * (size_t)(K + 1));
     h = fnv1a(ent_off, sizeof(int64_t) * (size_t)(K + 1), h);
-    return run(ctx, P, true, tc, (cudaStream_t)stream, &table, h);
+    std::vector<int64_t> offs(site_off, site_off + K + 1);
+    offs.insert(offs.end(), ent_off, ent_off + K + 1);
+    return run(ctx, P, true, tc, (cudaStream_t)stream, &table, h, true, &offs);
 }
 
 ccl_status ccl_sync(ccl_context *ctx, void *stream, int64_t timeout_ms) {

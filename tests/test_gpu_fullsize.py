@@ -1,0 +1,45 @@
+"""Full-size parity: the single-instance workloads at their stated sizes, in
+the launch configuration the benchmark times (default options, graph replay),
+compared site by site with the oracle's union-find labels.
+
+  honeycomb 256x256 cells (131,072 sites), p = 0.6527
+  triangle 4096x4096 (16,777,216 sites), p = 0.3473
+  Bethe z=3, 24 shells, random position (50,331,646 sites), p = 0.5
+  triangle 16384x16384 (268,435,456 sites), p = 0.3473  (the largest served instance)
+"""
+import numpy as np
+import pytest
+import torch
+
+import lattices as L
+import oracle
+import paper_1603_08357_gb300 as ccl
+from ccl_testutil import DEV, to_dev
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "hc256": dict(kind="honeycomb", L=256, p=0.6527, seed=1),
+    "tri4096": dict(kind="triangle", L=4096, p=0.3473, seed=2),
+    "bethe24": dict(kind="cayley", z=3, shells=24, p=0.5, seed=3, perm_seed=3),
+    "tri16384": dict(kind="triangle", L=16384, p=0.3473, seed=5),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_full_size_matches_oracle(ctx, name):
+    lat = L.make_instance(CASES[name])
+    rp, ci, bits = to_dev(lat)
+    out = torch.empty(lat.n, dtype=torch.int32, device=DEV)
+    for _ in range(2):                       # first call captures, second replays the graph
+        out.fill_(-1)
+        assert ccl.ccl_label(ctx, lat.n, lat.nnz, rp, ci, bits, out) == ccl.CCL_OK
+        assert ccl.ccl_sync(ctx) == ccl.CCL_OK
+    got = out.cpu().numpy()
+    del rp, ci, bits, out
+    torch.cuda.empty_cache()
+    want = oracle.uf_label(lat)
+    assert np.array_equal(got, want), int(np.count_nonzero(got != want))
+    if lat.kind == "cayley":
+        # forest identity at full size: clusters = sites - open bonds
+        assert np.count_nonzero(got == np.arange(lat.n)) == lat.n - lat.n_open_bonds

@@ -243,3 +243,21 @@ def test_two_streams_two_contexts():
     assert np.array_equal(ob.cpu().numpy(), oracle.uf_label(b))
     ccl.ccl_context_destroy(c1)
     ccl.ccl_context_destroy(c2)
+
+
+def test_graph_replay_keyed_on_sizes(ctx):
+    """Same device buffers and chunk count, different n / nnz: the cached graph
+    of the first call must not be replayed for the second."""
+    a = L.random_graph(40, 60, 1)
+    b = L.random_graph(50, 90, 2)
+    rp = torch.zeros(64, dtype=torch.int32, device=DEV)
+    ci = torch.zeros(256, dtype=torch.int32, device=DEV)
+    bits = torch.zeros(8, dtype=torch.int32, device=DEV)
+    out = torch.zeros(64, dtype=torch.int32, device=DEV)
+    for lat in (a, b, a, b):
+        rp[:lat.n + 1] = torch.from_numpy(lat.row_ptr).to(DEV)
+        ci[:lat.nnz] = torch.from_numpy(lat.col_idx).to(DEV)
+        bits[:lat.open_bits.size] = torch.from_numpy(lat.open_bits.view(np.int32)).to(DEV)
+        assert ccl.ccl_label(ctx, lat.n, lat.nnz, rp, ci, bits, out) == ccl.CCL_OK
+        assert ccl.ccl_sync(ctx) == ccl.CCL_OK
+        assert np.array_equal(out[:lat.n].cpu().numpy(), oracle.uf_label(lat))
