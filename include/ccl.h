@@ -166,6 +166,10 @@ typedef struct {
     int64_t nnz;              /* CSR entries read */
     int32_t n_inst;           /* instances */
     int32_t used_graph;       /* 1 if the call replayed a captured CUDA graph */
+    /* step (iii) work counters, filled only by a library built with
+       -DCCL_DEVICE_STATS (else 0): label loads of the root chases, atomicMin
+       operations of the merge loops, warp iterations of the reduction */
+    int64_t chase_loads, merge_atomics, reduce_iterations;
 } ccl_run_stats;
 
 CCL_API ccl_status ccl_get_stats(ccl_context *ctx, ccl_run_stats *stats);

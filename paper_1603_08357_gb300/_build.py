@@ -20,6 +20,10 @@ SOURCES = ["ccl_api.cu", "ccl_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I" + os.path.join(ROOT, "include")]
+# CCL_DEVICE_STATS=1 in the environment builds the counting variant of the
+# reduction kernel (work counters in ccl_run_stats)
+if os.environ.get("CCL_DEVICE_STATS") == "1":
+    FLAGS.append("-DCCL_DEVICE_STATS")
 _lock = threading.Lock()
 
 

@@ -46,7 +46,9 @@ class CclError(RuntimeError):
 
 class ccl_run_stats(ctypes.Structure):
     _fields_ = [("residual_pairs", ctypes.c_int64), ("n_sites", ctypes.c_int64),
-                ("nnz", ctypes.c_int64), ("n_inst", ctypes.c_int32), ("used_graph", ctypes.c_int32)]
+                ("nnz", ctypes.c_int64), ("n_inst", ctypes.c_int32), ("used_graph", ctypes.c_int32),
+                ("chase_loads", ctypes.c_int64), ("merge_atomics", ctypes.c_int64),
+                ("reduce_iterations", ctypes.c_int64)]
 
 
 class ccl_server_config(ctypes.Structure):

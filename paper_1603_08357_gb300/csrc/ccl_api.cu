@@ -117,9 +117,6 @@ struct DeviceGuard {
     }
 };
 
-size_t stage_bytes(int threads) {
-    return (size_t)(threads / 32) * (kStageEntries + kStageWords) * sizeof(int32_t);
-}
 
 int blocks_per_sm(ccl_context *ctx, int kernel_id, int threads) {
     auto key = std::make_pair(kernel_id, threads);
@@ -128,8 +125,8 @@ int blocks_per_sm(ccl_context *ctx, int kernel_id, int threads) {
     int nb = 1;
     cudaError_t e = cudaSuccess;
     switch (kernel_id) {
-        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init<false>, threads, stage_bytes(threads)); break;
-        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init<true>, threads, stage_bytes(threads)); break;
+        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init<false>, kInitThreads, kInitSmem); break;
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init<true>, kInitThreads, kInitSmem); break;
         case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_analysis<false>, threads, 0); break;
         case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_analysis<true>, threads, 0); break;
         case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_reduce<false>, threads, 0); break;
@@ -148,6 +145,12 @@ int64_t grid_for(ccl_context *ctx, int kernel_id, const TuneChoice &tc, int64_t 
     const int64_t wpb = tc.threads / 32;
     const int64_t need = (warps_needed + wpb - 1) / wpb;
     return std::max<int64_t>(1, std::min(g, need));
+}
+
+// step (i): fixed CTA shape, one CTA per tile at most
+int64_t grid_init(ccl_context *ctx, bool batched, int64_t n_tiles) {
+    const int per_sm = blocks_per_sm(ctx, batched ? 1 : 0, kInitThreads);
+    return std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * per_sm, n_tiles));
 }
 
 ccl_status ensure_workspace(ccl_context *ctx, int64_t q_slots, int64_t chunks) {
@@ -196,15 +199,14 @@ TuneChoice choice_for(ccl_context *ctx, int64_t n, int64_t nnz) {
 ccl_status enqueue_steps(ccl_context *ctx, const Params &P, bool batched, const TuneChoice &tc,
                          cudaStream_t s, bool profile) {
     const int T = tc.threads;
-    const size_t smem = stage_bytes(T);
-    const int64_t warps_chunks = P.n_chunks;
+    const int64_t warps_chunks = (P.n_chunks + kAnaChunks - 1) / kAnaChunks;
     const int64_t warps_groups = (P.n_chunks + 31) / 32;
-    CCL_CUDA(cudaMemsetAsync(P.counters, 0, sizeof(unsigned long long), s));
+    CCL_CUDA(cudaMemsetAsync(P.counters, 0, 4 * sizeof(unsigned long long), s));
     if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[0], s));
     if (batched) {
-        k_init<true><<<(unsigned)grid_for(ctx, 1, tc, warps_chunks), T, smem, s>>>(P);
+        k_init<true><<<(unsigned)grid_init(ctx, true, P.n_tiles), kInitThreads, kInitSmem, s>>>(P);
     } else {
-        k_init<false><<<(unsigned)grid_for(ctx, 0, tc, warps_chunks), T, smem, s>>>(P);
+        k_init<false><<<(unsigned)grid_init(ctx, false, P.n_tiles), kInitThreads, kInitSmem, s>>>(P);
     }
     CCL_CUDA(cudaGetLastError());
     if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[1], s));
@@ -282,7 +284,7 @@ bool stream_capturing(cudaStream_t s) {
 ccl_status run(ccl_context *ctx, Params P, bool batched, const TuneChoice &tc, cudaStream_t s,
                const std::vector<Inst> *table, uint64_t shape_hash, bool allow_graph = true,
                const std::vector<int64_t> *offsets = nullptr) {
-    for (int kid = 0; kid < 6; ++kid) (void)blocks_per_sm(ctx, kid, tc.threads);
+    for (int kid = 0; kid < 6; ++kid) (void)blocks_per_sm(ctx, kid, kid < 2 ? kInitThreads : tc.threads);
     ctx->last.used_graph = 0;
     const bool capturing = stream_capturing(s);
     if (ctx->profile || !ctx->use_graphs || capturing || !allow_graph) {
@@ -357,6 +359,18 @@ ccl_status run(ccl_context *ctx, Params P, bool batched, const TuneChoice &tc, c
     return CCL_OK;
 }
 
+// readable memory of the three input arrays of an instance (the whole
+// concatenated arrays for a batch)
+void set_bounds(Inst &I, const int32_t *rp, int64_t rp_len, const int32_t *ci, int64_t ci_len,
+                const uint32_t *bits, int64_t bits_len) {
+    I.rp_lo = rp;
+    I.rp_hi = rp + rp_len;
+    I.ci_lo = ci;
+    I.ci_hi = ci ? ci + ci_len : ci;
+    I.bits_lo = bits;
+    I.bits_hi = bits ? bits + bits_len : bits;
+}
+
 Params base_params(ccl_context *ctx, const TuneChoice &tc) {
     Params P;
     memset(&P, 0, sizeof(P));
@@ -387,13 +401,16 @@ ccl_status label_single(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t 
     Params P = base_params(ctx, tc);
     P.K = 1;
     P.n_chunks = chunks;
+    P.n_tiles = ((int64_t)n + kTileSites - 1) / kTileSites;
     P.one.row_ptr = row_ptr;
     P.one.col_idx = col_idx;
     P.one.bits = bits;
     P.one.labels = labels;
+    set_bounds(P.one, row_ptr, (int64_t)n + 1, col_idx, nnz, bits, (nnz + 31) / 32);
     P.one.bit_off = 0;
     P.one.q_off = 0;
     P.one.chunk_begin = 0;
+    P.one.tile_begin = 0;
     P.one.n = n;
     P.one.nnz = (int32_t)nnz;
     ctx->last.n_sites = n;
@@ -411,12 +428,14 @@ namespace ccl {
 // n, nnz filled in by the caller) in one pass of the four steps on stream s.
 // Used by the request loop, whose instances live in separate allocations.
 ccl_status label_instances(ccl_context *ctx, std::vector<Inst> &table, cudaStream_t s) {
-    int64_t chunks = 0, q = 0;
+    int64_t chunks = 0, q = 0, tiles = 0;
     for (Inst &I : table) {
         I.q_off = q;
         I.chunk_begin = chunks;
+        I.tile_begin = tiles;
         q += I.nnz;
         chunks += ((int64_t)I.n + kChunk - 1) / kChunk;
+        tiles += ((int64_t)I.n + kTileSites - 1) / kTileSites;
     }
     if (chunks == 0) return CCL_OK;
     DeviceGuard guard(ctx->device);
@@ -426,6 +445,7 @@ ccl_status label_instances(ccl_context *ctx, std::vector<Inst> &table, cudaStrea
     Params P = base_params(ctx, tc);
     P.K = (int32_t)table.size();
     P.n_chunks = chunks;
+    P.n_tiles = tiles;
     if (table.size() == 1) {
         P.one = table[0];
         return run(ctx, P, false, tc, s, nullptr, 0, false);
@@ -475,10 +495,10 @@ ccl_status ccl_context_create(ccl_context **out, int device) {
     // the opt-in shared memory of the staging buffers
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_init<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)stage_bytes(512));
+                                 (int)kInitSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_init<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)stage_bytes(512));
+                                 (int)kInitSmem);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         ccl_context_destroy(ctx);
@@ -591,7 +611,8 @@ ccl_status ccl_label_batched(ccl_context *ctx, int32_t K, const int64_t *site_of
     if (site_off[0] != 0 || ent_off[0] != 0) return CCL_ERR_INVALID_ARGUMENT;
     std::vector<Inst> table;
     table.reserve((size_t)K);
-    int64_t chunks = 0;
+    int64_t chunks = 0, tiles = 0;
+    const int64_t rp_len = site_off[K] + K, ci_len = ent_off[K], bits_len = (ent_off[K] + 31) / 32;
     for (int32_t k = 0; k < K; ++k) {
         const int64_t n = site_off[k + 1] - site_off[k];
         const int64_t nnz = ent_off[k + 1] - ent_off[k];
@@ -601,13 +622,16 @@ ccl_status ccl_label_batched(ccl_context *ctx, int32_t K, const int64_t *site_of
         I.col_idx = col_idx + ent_off[k];
         I.bits = bits;
         I.labels = labels + site_off[k];
+        set_bounds(I, row_ptr, rp_len, col_idx, ci_len, bits, bits_len);
         I.bit_off = ent_off[k];
         I.q_off = ent_off[k];
         I.chunk_begin = chunks;
+        I.tile_begin = tiles;
         I.n = (int32_t)n;
         I.nnz = (int32_t)nnz;
         table.push_back(I);
         chunks += (n + kChunk - 1) / kChunk;
+        tiles += (n + kTileSites - 1) / kTileSites;
     }
     const int64_t n_tot = site_off[K], nnz_tot = ent_off[K];
     if (n_tot > 0 && (!row_ptr || !labels)) return CCL_ERR_INVALID_ARGUMENT;
@@ -624,6 +648,7 @@ ccl_status ccl_label_batched(ccl_context *ctx, int32_t K, const int64_t *site_of
     Params P = base_params(ctx, tc);
     P.K = K;
     P.n_chunks = chunks;
+    P.n_tiles = tiles;
     if (K == 1) {
         P.one = table[0];
         return run(ctx, P, false, tc, (cudaStream_t)stream, nullptr, fnv1a(&P.one, sizeof(Inst)));
@@ -726,10 +751,13 @@ ccl_status ccl_get_stats(ccl_context *ctx, ccl_run_stats *out) {
     if (!ctx || !out) return CCL_ERR_INVALID_ARGUMENT;
     DeviceGuard guard(ctx->device);
     CCL_CUDA(cudaDeviceSynchronize());
-    unsigned long long pairs = 0;
-    CCL_CUDA(cudaMemcpy(&pairs, ctx->d_counters, sizeof(pairs), cudaMemcpyDeviceToHost));
+    unsigned long long c[4] = {0, 0, 0, 0};
+    CCL_CUDA(cudaMemcpy(c, ctx->d_counters, sizeof(c), cudaMemcpyDeviceToHost));
     *out = ctx->last;
-    out->residual_pairs = (int64_t)pairs;
+    out->residual_pairs = (int64_t)c[0];
+    out->chase_loads = (int64_t)c[1];
+    out->merge_atomics = (int64_t)c[2];
+    out->reduce_iterations = (int64_t)c[3];
     return CCL_OK;
 }
 

@@ -2,14 +2,18 @@
 // Komura, "A generalized GPU-based connected component labeling algorithm",
 // as sm_103a kernels over one or many instances.
 //
-// Work is cut into chunks of 32 consecutive sites of one instance; one warp
-// owns a chunk at a time, persistent warps stride over all chunks of all
-// instances. Step (i) stages a chunk's CSR segment (row pointers, column
-// indices and the words of open bits) in the warp's shared memory with
-// coalesced streaming loads and writes the chunk's residual pairs to a queue
-// slot range that is fixed by the chunk's first CSR entry, so no global atomic
-// counter is needed; step (iii) walks 32 chunk records per warp and
-// flattens their pairs across the lanes.
+// Sites are grouped in chunks of 32 consecutive sites of one instance and
+// chunks in tiles of kTileSites sites.
+//  * Step (i) streams the CSR input: per CTA one producer warp moves each
+//    tile's row pointers, column indices and bit words into shared memory with
+//    bulk asynchronous copies (cp.async.bulk, completion on mbarriers, a ring
+//    of kStages stages); eight consumer warps scan the rows and write the
+//    labels, the chunk records and the residual pairs. A chunk's pairs go to
+//    queue slots fixed by its first CSR entry, so no global counter is needed.
+//  * Steps (ii)/(iv) and (iii) chase label chains. Chains have a long tail,
+//    so instead of one chain per lane per round a lane that finishes takes
+//    the next site (pair) of its warp's window: the warp's loads stay busy
+//    until the window is drained.
 #pragma once
 #include <stdint.h>
 #include <cuda_runtime.h>
@@ -20,9 +24,6 @@ namespace ccl {
 
 // ---------------------------------------------------------------------------
 // small helpers
-
-__device__ __forceinline__ int32_t ld_stream(const int32_t *p) { return __ldcs(p); }
-__device__ __forceinline__ uint32_t ld_stream(const uint32_t *p) { return __ldcs(p); }
 
 __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 #pragma unroll
@@ -37,7 +38,7 @@ __device__ __forceinline__ void raise_err(unsigned *err, unsigned bit) {
     if ((*(volatile unsigned *)err & bit) == 0) atomicOr(err, bit);
 }
 
-// instance owning global chunk c: largest k with insts[k].chunk_begin <= c
+// largest k with insts[k].chunk_begin <= c (instances ordered)
 __device__ __forceinline__ int find_inst(const Params &P, int64_t c) {
     int lo = 0, hi = P.K - 1;
     while (lo < hi) {
@@ -47,52 +48,86 @@ __device__ __forceinline__ int find_inst(const Params &P, int64_t c) {
     return lo;
 }
 
+__device__ __forceinline__ int find_inst_tile(const Params &P, int64_t t) {
+    int lo = 0, hi = P.K - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&P.insts[mid].tile_begin) <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 template <bool kBatched>
 __device__ __forceinline__ Inst inst_of(const Params &P, int k) {
     if (!kBatched) return P.one;
-    Inst I;
-    const Inst *s = &P.insts[k];
-    I.row_ptr = (const int32_t *)__ldg((const unsigned long long *)&s->row_ptr);
-    I.col_idx = (const int32_t *)__ldg((const unsigned long long *)&s->col_idx);
-    I.bits = (const uint32_t *)__ldg((const unsigned long long *)&s->bits);
-    I.labels = (int32_t *)__ldg((const unsigned long long *)&s->labels);
-    I.bit_off = __ldg(&s->bit_off);
-    I.q_off = __ldg(&s->q_off);
-    I.chunk_begin = __ldg(&s->chunk_begin);
-    I.n = __ldg(&s->n);
-    I.nnz = __ldg(&s->nnz);
-    return I;
+    return P.insts[k];
 }
 
-// Follows label[x] to its root (label[r] == r). Loads go to L2 (.cg) so that
-// values written by atomics on other SMs are seen. Chains strictly decrease,
-// so a walk longer than n means a corrupt array: flag it and stop.
-__device__ __forceinline__ int32_t find_root_cg(const int32_t *L, int32_t x, int32_t cap,
-                                                unsigned *err) {
-    for (int32_t it = 0;; ++it) {
-        int32_t p = __ldcg(L + x);
-        if (p == x) return x;
-        x = p;
-        if (it > cap) { raise_err(err, kErrNonconv); return x; }
-    }
+// ---------------------------------------------------------------------------
+// mbarrier / bulk-copy primitives (inline PTX)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Algorithm 1, atomicMin loop, for two roots r1 > r2 found by the chase.
-// Each atomicMin puts r2 under r1; a displaced parent `old` is merged next.
-// `old == r1` means r1 was still a root, so nothing was displaced.
-__device__ __forceinline__ void merge_roots(int32_t *L, int32_t r1, int32_t r2, int32_t cap,
-                                            unsigned *err) {
-    for (int32_t it = 0;; ++it) {
-        int32_t old = atomicMin(L + r1, r2);
-        if (old == r2 || old == r1) return;
-        if (old > r2) {
-            r1 = old;
-        } else {
-            r1 = r2;
-            r2 = old;
-        }
-        if (it > cap) { raise_err(err, kErrNonconv); return; }
-    }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
+                 ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}"
+                 ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase of `parity` to complete; gives up after a bounded
+// number of polls (each poll itself suspends for a hardware-bounded time).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    for (uint32_t it = 0; it < (1u << 22); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// 1-D bulk copy global -> shared, completing `bytes` on the mbarrier.
+// dst, src and bytes are multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+// The 16-byte aligned span covering elements [lo, hi) of the 4-byte array
+// `arr`, clipped to the readable memory [mlo, mhi). Returns the element range
+// [c_lo, c_hi) it covers (relative to arr; may extend past [lo, hi)), or an
+// empty range if nothing can be copied or it exceeds `cap` elements.
+__device__ __forceinline__ void copy_window(const void *arr, int64_t lo, int64_t hi, const void *mlo,
+                                            const void *mhi, int cap, int64_t &c_lo, int64_t &c_hi) {
+    const uintptr_t base = (uintptr_t)arr;
+    uintptr_t a = (base + 4 * (uintptr_t)lo) & ~(uintptr_t)15;
+    uintptr_t b = (base + 4 * (uintptr_t)hi + 15) & ~(uintptr_t)15;
+    const uintptr_t l = ((uintptr_t)mlo + 15) & ~(uintptr_t)15;
+    const uintptr_t h = (uintptr_t)mhi & ~(uintptr_t)15;
+    if (a < l) a = l;
+    if (b > h) b = h;
+    if (hi <= lo || b <= a || (b - a) / 4 > (uintptr_t)cap) { c_lo = c_hi = lo; return; }
+    c_lo = ((intptr_t)a - (intptr_t)base) / 4;
+    c_hi = ((intptr_t)b - (intptr_t)base) / 4;
 }
 
 // ---------------------------------------------------------------------------
@@ -100,138 +135,324 @@ __device__ __forceinline__ void merge_roots(int32_t *L, int32_t r1, int32_t r2, 
 // label[i] = min(lower) or i; every other entry of `lower` (one occurrence of
 // the minimum removed) is a residual pair (i, j).
 
+// tiles of CTA b: the contiguous band [band_lo, band_hi)
+__device__ __forceinline__ void cta_band(int64_t n_tiles, int64_t &band_lo, int64_t &band_hi) {
+    const int64_t per = (n_tiles + gridDim.x - 1) / gridDim.x;
+    band_lo = min((int64_t)blockIdx.x * per, n_tiles);
+    band_hi = min(band_lo + per, n_tiles);
+}
+
 template <bool kBatched>
-__global__ void __launch_bounds__(512) k_init(Params P) {
-    extern __shared__ int32_t s_stage[];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    int32_t *sc = s_stage + wib * (kStageEntries + kStageWords);
-    uint32_t *sb = (uint32_t *)(sc + kStageEntries);
-    unsigned long long my_pairs = 0;
-
-    for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; c < P.n_chunks; c += nwarps) {
-        const int k = kBatched ? find_inst(P, c) : 0;
+__device__ __forceinline__ void init_produce(const Params &P, Stage *st, uint64_t *full,
+                                             uint64_t *empty) {
+    int64_t band_lo, band_hi;
+    cta_band(P.n_tiles, band_lo, band_hi);
+    int64_t t_local = 0;
+    for (int64_t tile = band_lo; tile < band_hi; ++tile, ++t_local) {
+        const int s = (int)(t_local % kStages);
+        const int64_t use = t_local / kStages;
+        if (use > 0 && !mbar_wait_bounded(&empty[s], (uint32_t)((use - 1) & 1))) {
+            raise_err(P.err, kErrNonconv);
+            break;
+        }
+        const int k = kBatched ? find_inst_tile(P, tile) : 0;
         const Inst I = inst_of<kBatched>(P, k);
-        const int32_t n = I.n;
-        const int32_t s0 = (int32_t)((c - I.chunk_begin) * kChunk);
-        const int32_t i = s0 + lane;
-        const int32_t slast = min(s0 + kChunk, n);          // one past the chunk's last site
-        // lane l: start of its row; lanes past the end read row_ptr[slast]
-        int32_t a = ld_stream(I.row_ptr + min(i, slast));
-        int32_t tail = 0;
-        if (lane == 0) tail = ld_stream(I.row_ptr + slast);
-        tail = __shfl_sync(kFull, tail, 0);
-        int32_t a_next = __shfl_down_sync(kFull, a, 1);
-        if (lane == 31) a_next = tail;
-        const bool ok = (a >= 0) && (a <= a_next) && (a_next <= I.nnz);
-        const bool all_ok = __all_sync(kFull, ok);
-        if (lane == 0) {
-            if (s0 == 0 && a != 0) raise_err(P.err, kErrShape);
-            if (slast == n && tail != I.nnz) raise_err(P.err, kErrShape);
+        StageHdr h;
+        h.k = k;
+        h.s0 = (int32_t)((tile - I.tile_begin) * kTileSites);
+        h.ts = min(kTileSites, I.n - h.s0);
+        h.e0 = __ldcs(I.row_ptr + h.s0);
+        h.e1 = __ldcs(I.row_ptr + h.s0 + h.ts);
+        h.status = (h.e0 < 0 || h.e1 < h.e0 || h.e1 > I.nnz) ? 1 : 0;
+        int64_t lo, hi;
+        copy_window(I.row_ptr, h.s0, (int64_t)h.s0 + h.ts + 1, I.rp_lo, I.rp_hi, kRpBuf, lo, hi);
+        h.rp_lo = (int32_t)lo;
+        h.rp_hi = (int32_t)hi;
+        if (h.status == 0) {
+            copy_window(I.col_idx, h.e0, h.e1, I.ci_lo, I.ci_hi, kColBuf, lo, hi);
+            h.ci_lo = (int32_t)lo;
+            h.ci_hi = (int32_t)hi;
+            const int64_t w0 = (I.bit_off + h.e0) >> 5;
+            const int64_t w1 = h.e1 > h.e0 ? ((I.bit_off + h.e1 - 1) >> 5) + 1 : w0;
+            copy_window(I.bits, w0, w1, I.bits_lo, I.bits_hi, kBitBuf, h.w_lo, h.w_hi);
+        } else {
+            h.ci_lo = h.ci_hi = 0;
+            h.w_lo = h.w_hi = 0;
         }
-        if (!all_ok) {
-            if (lane == 0) raise_err(P.err, kErrIndex);
-            a = a_next = 0;
-        }
-        const int32_t beg = __shfl_sync(kFull, a, 0);
-        const int32_t end = all_ok ? tail : 0;
-        const int32_t E = end - beg;
-        const bool staged = E <= kStageEntries;
-        const int64_t g0 = I.bit_off + beg;
-        const int64_t w0 = g0 >> 5;
-        if (staged) {
-            for (int t = lane; t < E; t += 32) sc[t] = ld_stream(I.col_idx + beg + t);
-            const int nwords = E > 0 ? (int)(((I.bit_off + end - 1) >> 5) - w0 + 1) : 0;
-            for (int t = lane; t < nwords; t += 32) sb[t] = ld_stream(I.bits + w0 + t);
-        }
-        __syncwarp();
+        st[s].h = h;
+        const uint32_t b_rp = 4u * (uint32_t)(h.rp_hi - h.rp_lo);
+        const uint32_t b_ci = 4u * (uint32_t)(h.ci_hi - h.ci_lo);
+        const uint32_t b_bw = 4u * (uint32_t)(h.w_hi - h.w_lo);
+        mbar_arrive_expect_tx(&full[s], b_rp + b_ci + b_bw);
+        if (b_rp) bulk_g2s(st[s].rp, I.row_ptr + h.rp_lo, b_rp, &full[s]);
+        if (b_ci) bulk_g2s(st[s].ci, I.col_idx + h.ci_lo, b_ci, &full[s]);
+        if (b_bw) bulk_g2s(st[s].bw, I.bits + h.w_lo, b_bw, &full[s]);
+    }
+}
 
-        int32_t m = INT32_MAX, mpos = -1, cnt = 0;
-        bool bad = false;
-        for (int32_t e = a; e < a_next; ++e) {
-            const int64_t g = I.bit_off + e;
-            int32_t j;
-            uint32_t w;
-            if (staged) { j = sc[e - beg]; w = sb[(g >> 5) - w0]; }
-            else { j = __ldg(I.col_idx + e); w = __ldg(I.bits + (g >> 5)); }
-            if ((uint32_t)j >= (uint32_t)n) { bad = true; continue; }
-            if (((w >> (g & 31)) & 1u) && j < i) {
-                ++cnt;
-                if (j < m) { m = j; mpos = e; }
+// General scan of one lane's row (rows longer than kRowRegs, or parts of the
+// input outside the shared-memory copy): per-entry bounds-checked reads.
+__device__ __forceinline__ void scan_row_general(const Stage &S, const Inst &I, int32_t a, int32_t a_next,
+                                                 int32_t i, int32_t &m, int32_t &mk, int32_t &cnt,
+                                                 bool &bad) {
+    const StageHdr &h = S.h;
+    for (int32_t e = a; e < a_next; ++e) {
+        const int64_t ge = I.bit_off + e;
+        const int32_t j = (e >= h.ci_lo && e < h.ci_hi) ? S.ci[e - h.ci_lo] : __ldg(I.col_idx + e);
+        const int64_t we = ge >> 5;
+        const uint32_t w = (we >= h.w_lo && we < h.w_hi) ? S.bw[we - h.w_lo] : __ldg(I.bits + we);
+        bad |= (uint32_t)j >= (uint32_t)I.n;
+        if (((w >> (ge & 31)) & 1u) && (uint32_t)j < (uint32_t)i) {
+            ++cnt;
+            if (j < m) { m = j; mk = e; }
+        }
+    }
+}
+
+// One chunk of 32 sites. `late` = the last tile of this CTA's band whose
+// labels are final and visible here (tiles at least kStages back), `band_lo`
+// = the band's first tile: a site whose smallest open lower neighbour m lies
+// in a tile in [band_lo, late] takes label[m] (the root of m's tree after
+// steps (i)/(ii)) instead of m, which shortcuts the chain step (ii) would walk.
+template <bool kBatched>
+__device__ __forceinline__ void init_consume_chunk(const Params &P, const Stage &S, const Inst &I,
+                                                   int cc, int lane, int64_t band_lo, int64_t late,
+                                                   unsigned long long &my_pairs) {
+    const StageHdr &h = S.h;
+    const int32_t n = I.n;
+    const int32_t s0 = h.s0 + cc * kChunk;
+    const int32_t i = s0 + lane;
+    const int32_t slast = min(s0 + kChunk, n);
+    int32_t a, a_next;
+    if (s0 >= h.rp_lo && slast < h.rp_hi) {
+        a = S.rp[min(i, slast) - h.rp_lo];
+        a_next = S.rp[min(i + 1, slast) - h.rp_lo];
+    } else {
+        a = __ldcs(I.row_ptr + min(i, slast));
+        a_next = __ldcs(I.row_ptr + min(i + 1, slast));
+    }
+    const bool ok = h.status == 0 && a >= h.e0 && a <= a_next && a_next <= h.e1;
+    const bool all_ok = __all_sync(kFull, ok);
+    if (lane == 0) {
+        if (s0 == 0 && a != 0) raise_err(P.err, kErrShape);
+        if (!all_ok) raise_err(P.err, kErrIndex);
+    }
+    if (lane == 31 && slast == n && a_next != I.nnz) raise_err(P.err, kErrShape);
+    if (!all_ok) a = a_next = 0;            // rows of a corrupt chunk are read as empty
+    const int32_t beg = __shfl_sync(kFull, a, 0);
+    const int32_t end = __shfl_sync(kFull, a_next, 31);
+    const int32_t deg = a_next - a;
+    const int32_t dmax = __reduce_max_sync(kFull, (uint32_t)deg);
+    const int64_t rb0 = I.bit_off - (h.w_lo << 5);      // stage-relative bit of entry 0
+    const bool fast = dmax <= kRowRegs && beg >= h.ci_lo && end <= h.ci_hi && rb0 + beg >= 0 &&
+                      rb0 + end <= 32 * (h.w_hi - h.w_lo);
+    int32_t m = INT32_MAX, cnt = 0;
+    int32_t mk = -1;
+    uint32_t resmask = 0;
+    bool bad = false;
+    if (fast) {
+        const int32_t* col = S.ci + (a - h.ci_lo);
+        uint32_t win = 0;
+        if (deg > 0) {
+            const int32_t rel = (int32_t)(rb0 + a);
+            win = __funnelshift_r(S.bw[rel >> 5], S.bw[(rel + deg - 1) >> 5], (uint32_t)rel & 31u);
+        }
+        uint32_t lowmask = 0, jmax = 0;
+#pragma unroll
+        for (int t = 0; t < kRowRegs; ++t) {
+            if (t >= dmax) break;
+            if (t < deg) {
+                const int32_t j = col[t];
+                jmax = max(jmax, (uint32_t)j);
+                if (((win >> t) & 1u) && (uint32_t)j < (uint32_t)i) {
+                    lowmask |= 1u << t;
+                    if (j < m) { m = j; mk = t; }
+                }
             }
         }
-        if (bad) raise_err(P.err, kErrIndex);
-        if (i < n) I.labels[i] = cnt ? m : i;
+        bad = jmax >= (uint32_t)n;
+        cnt = __popc(lowmask);
+        resmask = cnt ? (lowmask & ~(1u << mk)) : 0u;
+    } else {
+        scan_row_general(S, I, a, a_next, i, m, mk, cnt, bad);
+    }
+    if (bad) raise_err(P.err, kErrIndex);
+    int32_t lab = cnt ? m : i;
+    if (cnt) {
+        const int64_t mt = I.tile_begin + m / kTileSites;
+        if (mt >= band_lo && mt <= late) lab = __ldcg(I.labels + m);
+    }
+    if (i < n) I.labels[i] = lab;
 
-        const int r = cnt > 1 ? cnt - 1 : 0;
-        const int incl = warp_incl_scan(r, lane);
-        const int total = __shfl_sync(kFull, incl, 31);
-        const int64_t qbeg = I.q_off + beg;
-        if (r > 0) {
-            int64_t slot = qbeg + (incl - r);
+    const int r = cnt > 1 ? cnt - 1 : 0;
+    const int incl = warp_incl_scan(r, lane);
+    const int total = __shfl_sync(kFull, incl, 31);
+    const int64_t qbeg = I.q_off + beg;
+    if (r > 0) {
+        int64_t slot = qbeg + (incl - r);
+        if (fast) {
+            const int32_t* col = S.ci + (a - h.ci_lo);
+            while (resmask) {
+                const int t = __ffs(resmask) - 1;
+                resmask &= resmask - 1;
+                P.q[slot++] = make_int2(i, col[t]);
+            }
+        } else {
             for (int32_t e = a; e < a_next; ++e) {
-                const int64_t g = I.bit_off + e;
-                int32_t j;
-                uint32_t w;
-                if (staged) { j = sc[e - beg]; w = sb[(g >> 5) - w0]; }
-                else { j = __ldg(I.col_idx + e); w = __ldg(I.bits + (g >> 5)); }
-                if ((uint32_t)j >= (uint32_t)n) continue;
-                if (((w >> (g & 31)) & 1u) && j < i && e != mpos) P.q[slot++] = make_int2(i, j);
+                const int64_t ge = I.bit_off + e;
+                const int32_t j = (e >= h.ci_lo && e < h.ci_hi) ? S.ci[e - h.ci_lo] : __ldg(I.col_idx + e);
+                const int64_t we = ge >> 5;
+                const uint32_t w = (we >= h.w_lo && we < h.w_hi) ? S.bw[we - h.w_lo] : __ldg(I.bits + we);
+                if (((w >> (ge & 31)) & 1u) && (uint32_t)j < (uint32_t)i && e != mk)
+                    P.q[slot++] = make_int2(i, j);
             }
         }
-        if (lane == 0) {
-            ChunkRec rc;
-            rc.qbeg = qbeg;
-            rc.cnt = total;
-            rc.inst = k;
-            P.rec[c] = rc;
-            my_pairs += (unsigned long long)total;
+    }
+    if (lane == 0) {
+        ChunkRec rc;
+        rc.qbeg = qbeg;
+        rc.cnt = total;
+        rc.inst = h.k;
+        P.rec[I.chunk_begin + s0 / kChunk] = rc;
+        my_pairs += (unsigned long long)total;
+    }
+}
+
+template <bool kBatched>
+__global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
+    uint64_t *empty = full + kStages;
+    Stage *st = reinterpret_cast<Stage *>(smem_raw + 64);
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kInitConsumers);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (warp == kInitConsumers) {               // producer warp
+        if (lane == 0) init_produce<kBatched>(P, st, full, empty);
+        return;
+    }
+    unsigned long long my_pairs = 0;
+    int64_t band_lo, band_hi;
+    cta_band(P.n_tiles, band_lo, band_hi);
+    int64_t t_local = 0;
+    for (int64_t tile = band_lo; tile < band_hi; ++tile, ++t_local) {
+        const int s = (int)(t_local % kStages);
+        if (!mbar_wait_bounded(&full[s], (uint32_t)((t_local / kStages) & 1))) {
+            raise_err(P.err, kErrNonconv);
+            break;
+        }
+        const Stage &S = st[s];
+        const Inst I = inst_of<kBatched>(P, S.h.k);
+#pragma unroll 1
+        for (int q = 0; q < kChunksPerConsumer; ++q) {
+            const int cc = warp * kChunksPerConsumer + q;
+            if (cc * kChunk >= S.h.ts) break;
+            init_consume_chunk<kBatched>(P, S, I, cc, lane, band_lo, tile - kStages, my_pairs);
         }
         __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
     }
     if (lane == 0 && my_pairs) atomicAdd(P.counters, my_pairs);
 }
 
 // ---------------------------------------------------------------------------
 // Steps (ii) and (iv): analysis. Every site follows its label chain to the
-// root and stores the root. No atomics run concurrently with this kernel, and
+// root and stores the root. No atomics run concurrently with this kernel and
 // every value written is an ancestor of the site, so plain stores are safe.
+// A warp walks kAnaChunks chunks at once (one chain per lane per chunk) so
+// that their dependent loads overlap.
 
 template <bool kBatched>
 __global__ void __launch_bounds__(512) k_analysis(Params P) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < P.n_chunks;
-         c += nwarps) {
-        const int k = kBatched ? find_inst(P, c) : 0;
-        const Inst I = inst_of<kBatched>(P, k);
-        const int32_t i = (int32_t)((c - I.chunk_begin) * kChunk) + lane;
-        if (i >= I.n) continue;
-        int32_t *L = I.labels;
-        const int32_t l = L[i];
-        if (l == i) continue;
-        int32_t x = L[l];
-        if (x == l) continue;
-        for (int32_t it = 0;; ++it) {
-            const int32_t y = L[x];
-            if (y == x) break;
-            x = y;
-            if (it > I.n) { raise_err(P.err, kErrNonconv); break; }
+    const int64_t ngroups = (P.n_chunks + kAnaChunks - 1) / kAnaChunks;
+    for (int64_t gidx = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); gidx < ngroups;
+         gidx += nwarps) {
+        int32_t *L[kAnaChunks];
+        int32_t site[kAnaChunks], x[kAnaChunks], first[kAnaChunks];
+        int32_t cap = 0;
+        bool act[kAnaChunks];
+#pragma unroll
+        for (int u = 0; u < kAnaChunks; ++u) {
+            const int64_t c = gidx * kAnaChunks + u;
+            act[u] = false;
+            L[u] = nullptr;
+            site[u] = 0;
+            if (c < P.n_chunks) {
+                const int k = kBatched ? find_inst(P, c) : 0;
+                const Inst I = inst_of<kBatched>(P, k);
+                site[u] = (int32_t)((c - I.chunk_begin) * kChunk) + lane;
+                L[u] = I.labels;
+                cap = max(cap, I.n);
+                act[u] = site[u] < I.n;
+            }
         }
-        L[i] = x;
+#pragma unroll
+        for (int u = 0; u < kAnaChunks; ++u) {
+            x[u] = act[u] ? L[u][site[u]] : 0;
+            first[u] = x[u];
+            act[u] = act[u] && x[u] != site[u];
+        }
+        for (int32_t it = 0;; ++it) {
+            bool any = false;
+#pragma unroll
+            for (int u = 0; u < kAnaChunks; ++u) {
+                if (act[u]) {
+                    const int32_t y = L[u][x[u]];
+                    if (y == x[u]) act[u] = false;
+                    else { x[u] = y; any = true; }
+                }
+            }
+            if (!any) break;
+            if (it > cap) { raise_err(P.err, kErrNonconv); break; }
+        }
+#pragma unroll
+        for (int u = 0; u < kAnaChunks; ++u)
+            if (L[u] && x[u] != first[u] && site[u] < cap) L[u][site[u]] = x[u];
     }
 }
 
 // ---------------------------------------------------------------------------
-// Step (iii): label reduction, Algorithm 1 for every residual pair. A warp
-// takes 32 chunk records, prefix-sums their pair counts and spreads the pairs
-// over its lanes. After the chase, lanes whose (instance, r1, r2) coincide
-// elect one lane to run the atomicMin loop.
+// Step (iii): label reduction, Algorithm 1 for every residual pair (i, j).
+// A warp takes 32 chunk records and drains their pairs; a lane that finishes
+// a pair takes the next. For a pair the lane walks both label chains at once
+// (find the roots), points the first nodes of long chains at the root with
+// atomicMin (labels only decrease, so this never undoes a merge), then runs
+// Algorithm 1's atomicMin loop on the two roots.
+
+struct RedTask {
+    int32_t *L;
+    int32_t sa, sb, xa, xb, a0, b0, ha, hb, r1, r2, it, cap;
+    bool has, merge, da, db;
+};
+
+__device__ __forceinline__ void red_finish_chase(RedTask &t) {
+    // chain sa -> a0 -> ... -> xa: sa is stale if ha >= 2, a0 if ha >= 3
+    if (t.ha >= 2) atomicMin(t.L + t.sa, t.xa);
+    if (t.ha >= 3) atomicMin(t.L + t.a0, t.xa);
+    if (t.hb >= 2) atomicMin(t.L + t.sb, t.xb);
+    if (t.hb >= 3) atomicMin(t.L + t.b0, t.xb);
+    t.r1 = max(t.xa, t.xb);
+    t.r2 = min(t.xa, t.xb);
+    if (t.r1 == t.r2) t.has = false;
+    else { t.merge = true; t.it = 0; }
+}
 
 template <bool kBatched>
 __global__ void __launch_bounds__(512) k_reduce(Params P) {
     const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+#ifdef CCL_DEVICE_STATS
+    unsigned long long st_hops = 0, st_atom = 0, st_iter = 0;
+#endif
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t ngroups = (P.n_chunks + 31) / 32;
     for (int64_t gidx = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); gidx < ngroups;
@@ -242,8 +463,14 @@ __global__ void __launch_bounds__(512) k_reduce(Params P) {
         const int incl = warp_incl_scan(rc.cnt, lane);
         const int excl = incl - rc.cnt;
         const int total = __shfl_sync(kFull, incl, 31);
-        for (int base = 0; base < total; base += 32) {
-            const int p = base + lane;
+        if (total == 0) continue;
+        int next = 0;
+        RedTask t;
+        t.has = false;
+        for (;;) {
+            // refill
+            const unsigned need = __ballot_sync(kFull, !t.has);
+            const int p = next + __popc(need & lt);
             int src = 0;
 #pragma unroll
             for (int step = 16; step > 0; step >>= 1) {
@@ -253,36 +480,59 @@ __global__ void __launch_bounds__(512) k_reduce(Params P) {
             }
             const long long qb = __shfl_sync(kFull, (long long)rc.qbeg, src);
             const int ex_src = __shfl_sync(kFull, excl, src);
-            const int k = __shfl_sync(kFull, rc.inst, src);
-            const bool valid = p < total;
-            int32_t r1 = -1, r2 = -1;
-            int32_t *L = nullptr;
-            int32_t cap = 0;
-            if (valid) {
+            const int kk = __shfl_sync(kFull, rc.inst, src);
+            if (!t.has && p < total) {
                 const int2 pr = P.q[qb + (p - ex_src)];
                 if (kBatched) {
-                    L = (int32_t *)__ldg((const unsigned long long *)&P.insts[k].labels);
-                    cap = __ldg(&P.insts[k].n);
+                    t.L = P.insts[kk].labels;
+                    t.cap = P.insts[kk].n;
                 } else {
-                    L = P.one.labels;
-                    cap = P.one.n;
+                    t.L = P.one.labels;
+                    t.cap = P.one.n;
                 }
-                r1 = find_root_cg(L, __ldcg(L + pr.x), cap, P.err);
-                r2 = find_root_cg(L, __ldcg(L + pr.y), cap, P.err);
-                if (r1 < r2) { const int32_t t = r1; r1 = r2; r2 = t; }
+                t.sa = t.xa = pr.x;
+                t.sb = t.xb = pr.y;
+                t.ha = t.hb = 0;
+                t.da = t.db = false;
+                t.merge = false;
+                t.has = true;
             }
-            bool need = valid && r1 != r2;
-            if (P.dedup) {
-                const unsigned long long key = need
-                    ? (((unsigned long long)(uint32_t)r1 << 32) | (uint32_t)r2)
-                    : (0xffffffff00000000ull | (unsigned)lane);
-                unsigned peers = __match_any_sync(kFull, key);
-                if (kBatched) peers &= __match_any_sync(kFull, need ? k : -1 - lane);
-                need = need && ((__ffs(peers) - 1) == lane);
+            next = min(next + __popc(need), total);
+            // one step
+#ifdef CCL_DEVICE_STATS
+            st_iter++;
+            if (t.has) { if (t.merge) st_atom++; else st_hops += (!t.da) + (!t.db); }
+#endif
+            if (t.has) {
+                if (!t.merge) {
+                    if (!t.da) {
+                        const int32_t y = __ldcg(t.L + t.xa);
+                        if (y == t.xa) t.da = true;
+                        else { if (t.ha == 0) t.a0 = y; t.xa = y; ++t.ha; }
+                    }
+                    if (!t.db) {
+                        const int32_t y = __ldcg(t.L + t.xb);
+                        if (y == t.xb) t.db = true;
+                        else { if (t.hb == 0) t.b0 = y; t.xb = y; ++t.hb; }
+                    }
+                    if (t.ha > t.cap || t.hb > t.cap) { raise_err(P.err, kErrNonconv); t.has = false; }
+                    else if (t.da && t.db) red_finish_chase(t);
+                } else {
+                    const int32_t old = atomicMin(t.L + t.r1, t.r2);
+                    if (old == t.r2 || old == t.r1) t.has = false;
+                    else if (old > t.r2) t.r1 = old;
+                    else { t.r1 = t.r2; t.r2 = old; }
+                    if (++t.it > 2 * t.cap + 4) { raise_err(P.err, kErrNonconv); t.has = false; }
+                }
             }
-            if (need) merge_roots(L, r1, r2, 2 * cap + 4, P.err);
+            if (!__any_sync(kFull, t.has) && next >= total) break;
         }
     }
+#ifdef CCL_DEVICE_STATS
+    if (st_hops) atomicAdd(P.counters + 1, st_hops);
+    if (st_atom) atomicAdd(P.counters + 2, st_atom);
+    if (lane == 0 && st_iter) atomicAdd(P.counters + 3, st_iter);
+#endif
 }
 
 // ---------------------------------------------------------------------------

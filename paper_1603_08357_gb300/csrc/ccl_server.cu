@@ -228,6 +228,12 @@ void launch_batch(ccl_server *S, int slot, std::vector<std::shared_ptr<Req>> req
         I.col_idx = (const int32_t *)(r->d_mem + lay.ci);
         I.bits = (const uint32_t *)(r->d_mem + lay.bits);
         I.labels = (int32_t *)(r->d_mem + lay.lab);
+        I.rp_lo = r->d_mem;
+        I.rp_hi = r->d_mem + lay.total;     // one allocation holds all four arrays
+        I.ci_lo = I.rp_lo;
+        I.ci_hi = I.rp_hi;
+        I.bits_lo = I.rp_lo;
+        I.bits_hi = I.rp_hi;
         I.bit_off = 0;
         I.n = r->n;
         I.nnz = (int32_t)r->nnz;

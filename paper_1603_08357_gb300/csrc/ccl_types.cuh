@@ -6,14 +6,29 @@
 
 namespace ccl {
 
-constexpr int kChunk = 32;                 // sites per chunk (one warp)
-constexpr int kStageEntries = 256;         // CSR entries a warp can stage (8 per site)
-constexpr int kStageWords = kStageEntries / 32 + 2;
+constexpr int kChunk = 32;                 // sites per chunk (one warp's worth)
 constexpr unsigned kFull = 0xffffffffu;
+
+// step (i): one CTA = kInitConsumers consumer warps + 1 producer warp; the
+// producer streams tiles of kTileSites sites through kStages shared-memory
+// stages with bulk asynchronous copies
+constexpr int kTileSites = 1024;
+constexpr int kInitConsumers = 16;
+constexpr int kInitThreads = 32 * (kInitConsumers + 1);
+constexpr int kChunksPerConsumer = kTileSites / kChunk / kInitConsumers;
+constexpr int kStages = 3;
+constexpr int kColCap = 7168;              // column entries a stage holds (7 per site)
+constexpr int kRpBuf = kTileSites + 8;     // row pointers of a tile, + 16-byte rounding
+constexpr int kColBuf = kColCap + 8;
+constexpr int kBitBuf = kColCap / 32 + 12;
+constexpr int kRowRegs = 8;                // rows up to this degree are scanned in registers
+
+// steps (ii)/(iv): chunks a warp walks at once
+constexpr int kAnaChunks = 2;
 
 // latched device error bits
 constexpr unsigned kErrIndex = 1u;         // col_idx or row_ptr out of range
-constexpr unsigned kErrNonconv = 2u;       // iteration cap hit
+constexpr unsigned kErrNonconv = 2u;       // iteration cap hit, or a bounded wait expired
 constexpr unsigned kErrShape = 4u;         // row_ptr[0] != 0 or row_ptr[n] != nnz
 constexpr unsigned kErrAsym = 8u;          // validate: missing mirror entry
 
@@ -23,9 +38,13 @@ struct Inst {
     const int32_t *col_idx;    // local entry -> local site
     const uint32_t *bits;      // bit words; local entry e is bit bit_off + e
     int32_t *labels;           // n outputs
+    // readable memory around each input array: bulk copies round their
+    // ranges outward to 16 bytes but never leave [lo, hi)
+    const void *rp_lo, *rp_hi, *ci_lo, *ci_hi, *bits_lo, *bits_hi;
     int64_t bit_off;
     int64_t q_off;             // queue slot of local entry 0
     int64_t chunk_begin;       // first global chunk of the instance
+    int64_t tile_begin;        // first global tile of the instance
     int32_t n;
     int32_t nnz;
 };
@@ -43,10 +62,30 @@ struct Params {
     int32_t K;
     int32_t dedup;
     int64_t n_chunks;          // over all instances
+    int64_t n_tiles;           // over all instances
     ChunkRec *rec;             // [n_chunks]
     int2 *q;                   // residual pairs (i, j), slots indexed by global entry
     unsigned *err;
     unsigned long long *counters;   // [0] residual pairs
 };
+
+// Shared-memory stage of step (i).
+struct __align__(16) StageHdr {
+    int64_t w_lo, w_hi;        // bit words present: [w_lo, w_hi) relative to Inst::bits
+    int32_t k, s0, ts, e0, e1; // instance, first site, sites, entry range of the tile
+    int32_t rp_lo, rp_hi;      // row pointers present (indices relative to Inst::row_ptr)
+    int32_t ci_lo, ci_hi;      // column entries present (relative to Inst::col_idx)
+    int32_t status;            // 0 valid, 1 corrupt row pointers
+    int32_t pad_[3];
+};
+
+struct __align__(16) Stage {
+    StageHdr h;
+    int32_t rp[kRpBuf];
+    int32_t ci[kColBuf];
+    uint32_t bw[kBitBuf];
+};
+
+constexpr size_t kInitSmem = 64 + sizeof(Stage) * kStages;
 
 }  // namespace ccl
