@@ -81,12 +81,14 @@ CCL_API void ccl_context_destroy(ccl_context *ctx);
 /* Tunable options (ccl_set_option / ccl_get_option). */
 typedef enum {
     CCL_OPT_PRE_ANALYSIS = 0,  /* 1 (default): run step (ii) before (iii); 0: skip it */
-    CCL_OPT_BLOCK_THREADS = 1, /* threads per CTA of the labelling kernels (64..1024, multiple of 32) */
+    CCL_OPT_BLOCK_THREADS = 1, /* threads per CTA of the analysis kernel (64..512, multiple of 32) */
     CCL_OPT_USE_GRAPHS = 2,    /* 1 (default): replay captured CUDA graphs for repeated shapes */
     CCL_OPT_PROFILE = 3,       /* 1: record CUDA events between the steps (ccl_get_step_times);
                                   setting it restarts the averaging */
-    CCL_OPT_CTAS_PER_SM = 4,   /* persistent CTAs per SM; 0 (default) = occupancy maximum */
-    CCL_OPT_DEDUP = 5          /* 1 (default): warp-level dedupe of root pairs before atomics */
+    CCL_OPT_CTAS_PER_SM = 4,   /* persistent CTAs per SM of the analysis kernel; 0 (default) = occupancy maximum */
+    CCL_OPT_LINK_MODE = 5      /* step (iii): 0 (default) a root is linked under the other tree's
+                                  root, as in Algorithm 1; 1 under the node the other chain has
+                                  reached (same atomicMin loop, shorter walks on trees) */
 } ccl_option;
 
 CCL_API ccl_status ccl_set_option(ccl_context *ctx, int option, int64_t value);
@@ -184,11 +186,12 @@ CCL_API ccl_status ccl_get_step_times(ccl_context *ctx, float *ms, int32_t n);
 
 /*
  * ccl_autotune -- synchronous: times the labelling of the given instance under
- * candidate launch shapes (threads per CTA, CTAs per SM, step (ii) on/off)
+ * candidate settings (analysis threads per CTA, step (ii) on/off, link mode)
  * and keeps the fastest for instances of this size class (log2 of the site
- * count, mean degree rounded). Every candidate writes the same labels, so
- * `labels` holds the correct result afterwards. best_ms (optional) receives
- * the best time.
+ * count, mean degree rounded); the choice also becomes the context's
+ * options (ccl_get_option reports it). Every candidate writes the same labels,
+ * so `labels` holds the correct result afterwards. best_ms (optional)
+ * receives the best time.
  */
 CCL_API ccl_status ccl_autotune(ccl_context *ctx, int32_t n_sites, int64_t nnz, const int32_t *row_ptr,
                         const int32_t *col_idx, const uint32_t *open_bits, int32_t *labels,

@@ -34,7 +34,7 @@ CCL_OPT_BLOCK_THREADS = 1
 CCL_OPT_USE_GRAPHS = 2
 CCL_OPT_PROFILE = 3
 CCL_OPT_CTAS_PER_SM = 4
-CCL_OPT_DEDUP = 5
+CCL_OPT_LINK_MODE = 5
 
 
 class CclError(RuntimeError):
@@ -73,7 +73,8 @@ class ccl_server_stats(ctypes.Structure):
 
 
 def _load() -> ctypes.CDLL:
-    path = _build.LIB
+    # CCL_LIB may name another build of the same ABI (e.g. a counting build)
+    path = os.environ.get("CCL_LIB") or _build.LIB
     if not os.path.exists(path):
         raise ImportError(f"libccl.so is not built ({path}); run __graft_entry__.build() first")
     lib = ctypes.CDLL(path)
@@ -108,7 +109,7 @@ def _load() -> ctypes.CDLL:
 
 
 _lib = _load()
-LIB_PATH = _build.LIB
+LIB_PATH = os.environ.get("CCL_LIB") or _build.LIB
 
 
 # ----------------------------------------------------------------------------

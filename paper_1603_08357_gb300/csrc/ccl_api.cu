@@ -25,7 +25,7 @@ struct TuneChoice {
     int threads = 256;
     int ctas_per_sm = 0;
     int pre_analysis = 1;
-    int dedup = 1;
+    int link_mode = 0;
 };
 
 struct GraphEntry {
@@ -52,8 +52,9 @@ struct ccl_context {
     // workspace
     int2 *d_q = nullptr;
     int64_t q_cap = 0;
-    ChunkRec *d_rec = nullptr;
-    int64_t rec_cap = 0;
+    int32_t *d_qk = nullptr;     // instance of each pair (batched calls)
+    int64_t qk_cap = 0;
+    BandRec *d_band = nullptr;   // [kMaxBands]
     unsigned *d_err = nullptr;
     unsigned long long *d_counters = nullptr;
     // batched descriptor table (non-graph path)
@@ -147,21 +148,28 @@ int64_t grid_for(ccl_context *ctx, int kernel_id, const TuneChoice &tc, int64_t 
     return std::max<int64_t>(1, std::min(g, need));
 }
 
-// step (i): fixed CTA shape, one CTA per tile at most
+// step (i): fixed CTA shape; CTA b takes the band of tiles [b*per, (b+1)*per),
+// so launch just enough CTAs for every band to be non-empty
 int64_t grid_init(ccl_context *ctx, bool batched, int64_t n_tiles) {
     const int per_sm = blocks_per_sm(ctx, batched ? 1 : 0, kInitThreads);
-    return std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * per_sm, n_tiles));
+    int64_t g = std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * per_sm, n_tiles));
+    g = std::min<int64_t>(g, kMaxBands);
+    const int64_t per = (n_tiles + g - 1) / g;
+    return std::max<int64_t>(1, (n_tiles + per - 1) / per);
 }
 
-ccl_status ensure_workspace(ccl_context *ctx, int64_t q_slots, int64_t chunks) {
-    if (q_slots > ctx->q_cap || chunks > ctx->rec_cap) {
-        // growth invalidates every captured graph (they hold workspace pointers)
-        for (auto &g : ctx->graphs) {
-            if (g.exec) cudaGraphExecDestroy(g.exec);
-            if (g.d_insts) cudaFree(g.d_insts);
-        }
-        ctx->graphs.clear();
+void drop_graphs(ccl_context *ctx) {
+    for (auto &g : ctx->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.d_insts) cudaFree(g.d_insts);
     }
+    ctx->graphs.clear();
+}
+
+// Residual-pair queue: one slot per CSR entry of the call (a pair never needs
+// more), plus the per-pair instance for batched calls.
+ccl_status ensure_workspace(ccl_context *ctx, int64_t q_slots, bool batched) {
+    if (q_slots > ctx->q_cap || (batched && q_slots > ctx->qk_cap)) drop_graphs(ctx);  // graphs hold the pointers
     if (q_slots > ctx->q_cap) {
         if (ctx->d_q) cudaFree(ctx->d_q);
         ctx->d_q = nullptr;
@@ -170,13 +178,13 @@ ccl_status ensure_workspace(ccl_context *ctx, int64_t q_slots, int64_t chunks) {
         CCL_CUDA(cudaMalloc(&ctx->d_q, (size_t)want * sizeof(int2)));
         ctx->q_cap = want;
     }
-    if (chunks > ctx->rec_cap) {
-        if (ctx->d_rec) cudaFree(ctx->d_rec);
-        ctx->d_rec = nullptr;
-        ctx->rec_cap = 0;
-        const int64_t want = std::max<int64_t>(chunks, 1024);
-        CCL_CUDA(cudaMalloc(&ctx->d_rec, (size_t)want * sizeof(ChunkRec)));
-        ctx->rec_cap = want;
+    if (batched && q_slots > ctx->qk_cap) {
+        if (ctx->d_qk) cudaFree(ctx->d_qk);
+        ctx->d_qk = nullptr;
+        ctx->qk_cap = 0;
+        const int64_t want = std::max<int64_t>(q_slots, 1024);
+        CCL_CUDA(cudaMalloc(&ctx->d_qk, (size_t)want * sizeof(int32_t)));
+        ctx->qk_cap = want;
     }
     return CCL_OK;
 }
@@ -196,17 +204,21 @@ TuneChoice choice_for(ccl_context *ctx, int64_t n, int64_t nnz) {
 
 // Enqueues the four steps. All kernels read their sizes from Params, so the
 // sequence contains no host synchronisation and can be captured.
-ccl_status enqueue_steps(ccl_context *ctx, const Params &P, bool batched, const TuneChoice &tc,
+ccl_status enqueue_steps(ccl_context *ctx, const Params &P0, bool batched, const TuneChoice &tc,
                          cudaStream_t s, bool profile) {
     const int T = tc.threads;
-    const int64_t warps_chunks = (P.n_chunks + kAnaChunks - 1) / kAnaChunks;
-    const int64_t warps_groups = (P.n_chunks + 31) / 32;
+    const int64_t warps_chunks = (P0.n_chunks + kAnaChunks - 1) / kAnaChunks;
+    Params P = P0;
+    const int64_t g_init = grid_init(ctx, batched, P.n_tiles);
+    P.n_bands = (int32_t)g_init;
+    const int64_t g_red = (int64_t)ctx->num_sms * blocks_per_sm(ctx, batched ? 5 : 4, 256);
     CCL_CUDA(cudaMemsetAsync(P.counters, 0, 4 * sizeof(unsigned long long), s));
+    CCL_CUDA(cudaMemsetAsync(P.band, 0, (size_t)g_init * sizeof(BandRec), s));
     if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[0], s));
     if (batched) {
-        k_init<true><<<(unsigned)grid_init(ctx, true, P.n_tiles), kInitThreads, kInitSmem, s>>>(P);
+        k_init<true><<<(unsigned)g_init, kInitThreads, kInitSmem, s>>>(P);
     } else {
-        k_init<false><<<(unsigned)grid_init(ctx, false, P.n_tiles), kInitThreads, kInitSmem, s>>>(P);
+        k_init<false><<<(unsigned)g_init, kInitThreads, kInitSmem, s>>>(P);
     }
     CCL_CUDA(cudaGetLastError());
     if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[1], s));
@@ -216,8 +228,8 @@ ccl_status enqueue_steps(ccl_context *ctx, const Params &P, bool batched, const 
         CCL_CUDA(cudaGetLastError());
     }
     if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[2], s));
-    if (batched) k_reduce<true><<<(unsigned)grid_for(ctx, 5, tc, warps_groups), T, 0, s>>>(P);
-    else k_reduce<false><<<(unsigned)grid_for(ctx, 4, tc, warps_groups), T, 0, s>>>(P);
+    if (batched) k_reduce<true><<<(unsigned)g_red, 256, 0, s>>>(P);
+    else k_reduce<false><<<(unsigned)g_red, 256, 0, s>>>(P);
     CCL_CUDA(cudaGetLastError());
     if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[3], s));
     if (batched) k_analysis<true><<<(unsigned)grid_for(ctx, 3, tc, warps_chunks), T, 0, s>>>(P);
@@ -235,7 +247,7 @@ uint64_t fnv1a(const void *data, size_t bytes, uint64_t h = 1469598103934665603u
 
 bool same_choice(const TuneChoice &a, const TuneChoice &b) {
     return a.threads == b.threads && a.ctas_per_sm == b.ctas_per_sm &&
-           a.pre_analysis == b.pre_analysis && a.dedup == b.dedup;
+           a.pre_analysis == b.pre_analysis && a.link_mode == b.link_mode;
 }
 
 GraphEntry *find_graph(ccl_context *ctx, const GraphEntry &key) {
@@ -284,7 +296,8 @@ bool stream_capturing(cudaStream_t s) {
 ccl_status run(ccl_context *ctx, Params P, bool batched, const TuneChoice &tc, cudaStream_t s,
                const std::vector<Inst> *table, uint64_t shape_hash, bool allow_graph = true,
                const std::vector<int64_t> *offsets = nullptr) {
-    for (int kid = 0; kid < 6; ++kid) (void)blocks_per_sm(ctx, kid, kid < 2 ? kInitThreads : tc.threads);
+    for (int kid = 0; kid < 6; ++kid)
+        (void)blocks_per_sm(ctx, kid, kid < 2 ? kInitThreads : (kid >= 4 ? 256 : tc.threads));
     ctx->last.used_graph = 0;
     const bool capturing = stream_capturing(s);
     if (ctx->profile || !ctx->use_graphs || capturing || !allow_graph) {
@@ -374,9 +387,11 @@ void set_bounds(Inst &I, const int32_t *rp, int64_t rp_len, const int32_t *ci, i
 Params base_params(ccl_context *ctx, const TuneChoice &tc) {
     Params P;
     memset(&P, 0, sizeof(P));
-    P.dedup = tc.dedup;
-    P.rec = ctx->d_rec;
+    P.link_mode = tc.link_mode;
+    P.band = ctx->d_band;
     P.q = ctx->d_q;
+    P.qk = ctx->d_qk;
+    P.q_cap = ctx->q_cap;
     P.err = ctx->d_err;
     P.counters = ctx->d_counters;
     return P;
@@ -396,7 +411,7 @@ ccl_status label_single(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t 
                         const int32_t *col_idx, const uint32_t *bits, int32_t *labels,
                         cudaStream_t s, const TuneChoice &tc) {
     const int64_t chunks = ((int64_t)n + kChunk - 1) / kChunk;
-    ccl_status st = ensure_workspace(ctx, nnz, chunks);
+    ccl_status st = ensure_workspace(ctx, nnz, false);
     if (st != CCL_OK) return st;
     Params P = base_params(ctx, tc);
     P.K = 1;
@@ -439,7 +454,7 @@ ccl_status label_instances(ccl_context *ctx, std::vector<Inst> &table, cudaStrea
     }
     if (chunks == 0) return CCL_OK;
     DeviceGuard guard(ctx->device);
-    ccl_status st = ensure_workspace(ctx, q, chunks);
+    ccl_status st = ensure_workspace(ctx, q, table.size() > 1);
     if (st != CCL_OK) return st;
     const TuneChoice tc = ctx->opt;
     Params P = base_params(ctx, tc);
@@ -488,6 +503,7 @@ ccl_status ccl_context_create(ccl_context **out, int device) {
     cudaError_t e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_band, kMaxBands * sizeof(BandRec));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_counters, 4 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_counters, 0, 4 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
@@ -510,7 +526,7 @@ ccl_status ccl_context_create(ccl_context **out, int device) {
             int a, b, c, d;
             while (fscanf(f, "%lld %d %d %d %d", &cls, &a, &b, &c, &d) == 5) {
                 TuneChoice t;
-                t.threads = a; t.ctas_per_sm = b; t.pre_analysis = c; t.dedup = d;
+                t.threads = a; t.ctas_per_sm = b; t.pre_analysis = c; t.link_mode = d;
                 if (t.threads >= 64 && t.threads <= 512 && t.threads % 32 == 0) ctx->tune_table[cls] = t;
             }
             fclose(f);
@@ -528,7 +544,8 @@ void ccl_context_destroy(ccl_context *ctx) {
         if (g.d_insts) cudaFree(g.d_insts);
     }
     if (ctx->d_q) cudaFree(ctx->d_q);
-    if (ctx->d_rec) cudaFree(ctx->d_rec);
+    if (ctx->d_qk) cudaFree(ctx->d_qk);
+    if (ctx->d_band) cudaFree(ctx->d_band);
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->d_counters) cudaFree(ctx->d_counters);
     if (ctx->d_insts) cudaFree(ctx->d_insts);
@@ -560,7 +577,7 @@ ccl_status ccl_set_option(ccl_context *ctx, int option, int64_t value) {
             if (value < 0 || value > 64) return CCL_ERR_INVALID_ARGUMENT;
             ctx->opt.ctas_per_sm = (int)value;
             break;
-        case CCL_OPT_DEDUP: ctx->opt.dedup = value ? 1 : 0; break;
+        case CCL_OPT_LINK_MODE: ctx->opt.link_mode = value ? 1 : 0; break;
         default: return CCL_ERR_INVALID_ARGUMENT;
     }
     // explicit options take effect over any tuned entry
@@ -576,7 +593,7 @@ ccl_status ccl_get_option(ccl_context *ctx, int option, int64_t *value) {
         case CCL_OPT_USE_GRAPHS: *value = ctx->use_graphs; break;
         case CCL_OPT_PROFILE: *value = ctx->profile; break;
         case CCL_OPT_CTAS_PER_SM: *value = ctx->opt.ctas_per_sm; break;
-        case CCL_OPT_DEDUP: *value = ctx->opt.dedup; break;
+        case CCL_OPT_LINK_MODE: *value = ctx->opt.link_mode; break;
         default: return CCL_ERR_INVALID_ARGUMENT;
     }
     return CCL_OK;
@@ -585,8 +602,8 @@ ccl_status ccl_get_option(ccl_context *ctx, int option, int64_t *value) {
 ccl_status ccl_reserve(ccl_context *ctx, int64_t n_sites, int64_t nnz, int64_t n_chunks) {
     if (!ctx || n_sites < 0 || nnz < 0 || n_chunks < 0) return CCL_ERR_INVALID_ARGUMENT;
     DeviceGuard guard(ctx->device);
-    if (n_chunks == 0) n_chunks = (n_sites + kChunk - 1) / kChunk;
-    return ensure_workspace(ctx, nnz, n_chunks);
+    (void)n_chunks;
+    return ensure_workspace(ctx, nnz, true);
 }
 
 ccl_status ccl_label(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
@@ -642,7 +659,7 @@ ccl_status ccl_label_batched(ccl_context *ctx, int32_t K, const int64_t *site_of
     ctx->last.nnz = nnz_tot;
     if (chunks == 0) return CCL_OK;
     DeviceGuard guard(ctx->device);
-    ccl_status st = ensure_workspace(ctx, nnz_tot, chunks);
+    ccl_status st = ensure_workspace(ctx, nnz_tot, K > 1);
     if (st != CCL_OK) return st;
     const TuneChoice tc = choice_for(ctx, n_tot / K, nnz_tot / K);
     Params P = base_params(ctx, tc);
@@ -704,12 +721,7 @@ ccl_status ccl_label_host(ccl_context *ctx, int32_t n, int64_t nnz, const int32_
         if (ctx->d_host_in) cudaFree(ctx->d_host_in);
         ctx->d_host_in = nullptr;
         ctx->host_in_cap = 0;
-        // graphs may hold pointers into the old buffer
-        for (auto &g : ctx->graphs) {
-            if (g.exec) cudaGraphExecDestroy(g.exec);
-            if (g.d_insts) cudaFree(g.d_insts);
-        }
-        ctx->graphs.clear();
+        drop_graphs(ctx);    // graphs may hold pointers into the old buffer
         CCL_CUDA(cudaMalloc(&ctx->d_host_in, need));
         ctx->host_in_cap = (int64_t)need;
     }
@@ -798,13 +810,12 @@ ccl_status ccl_autotune(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t 
     float best_t = 1e30f;
     std::vector<TuneChoice> cands;
     for (int T : {128, 256, 512})
-        for (int C : {0, 2})
-            for (int pre = 0; pre < 2; ++pre)
-                for (int dd = 0; dd < 2; ++dd) {
-                    TuneChoice tc;
-                    tc.threads = T; tc.ctas_per_sm = C; tc.pre_analysis = pre; tc.dedup = dd;
-                    cands.push_back(tc);
-                }
+        for (int pre = 0; pre < 2; ++pre)
+            for (int lm = 0; lm < 2; ++lm) {
+                TuneChoice tc;
+                tc.threads = T; tc.ctas_per_sm = 0; tc.pre_analysis = pre; tc.link_mode = lm;
+                cands.push_back(tc);
+            }
     for (const TuneChoice &tc : cands) {
         float tmin = 1e30f;
         for (int rep = 0; rep < 4 && st == CCL_OK; ++rep) {
@@ -825,11 +836,12 @@ ccl_status ccl_autotune(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t 
     cudaEventDestroy(b);
     if (st != CCL_OK) return st;
     ctx->tune_table[size_class(n, nnz)] = best;
+    ctx->opt = best;     // also the default for other size classes
     if (const char *env = getenv("CCL_TUNE_CACHE")) {
         if (FILE *f = fopen(env, "w")) {
             for (auto &kv : ctx->tune_table)
                 fprintf(f, "%lld %d %d %d %d\n", (long long)kv.first, kv.second.threads,
-                        kv.second.ctas_per_sm, kv.second.pre_analysis, kv.second.dedup);
+                        kv.second.ctas_per_sm, kv.second.pre_analysis, kv.second.link_mode);
             fclose(f);
         }
     }

@@ -148,6 +148,7 @@ __device__ __forceinline__ void init_produce(const Params &P, Stage *st, uint64_
     int64_t band_lo, band_hi;
     cta_band(P.n_tiles, band_lo, band_hi);
     int64_t t_local = 0;
+    int64_t qband = 0;
     for (int64_t tile = band_lo; tile < band_hi; ++tile, ++t_local) {
         const int s = (int)(t_local % kStages);
         const int64_t use = t_local / kStages;
@@ -164,6 +165,11 @@ __device__ __forceinline__ void init_produce(const Params &P, Stage *st, uint64_
         h.e0 = __ldcs(I.row_ptr + h.s0);
         h.e1 = __ldcs(I.row_ptr + h.s0 + h.ts);
         h.status = (h.e0 < 0 || h.e1 < h.e0 || h.e1 > I.nnz) ? 1 : 0;
+        if (t_local == 0) {
+            qband = I.q_off + (h.status ? 0 : h.e0);
+            P.band[blockIdx.x].qbase = qband;
+        }
+        h.qband = qband;
         int64_t lo, hi;
         copy_window(I.row_ptr, h.s0, (int64_t)h.s0 + h.ts + 1, I.rp_lo, I.rp_hi, kRpBuf, lo, hi);
         h.rp_lo = (int32_t)lo;
@@ -217,6 +223,7 @@ __device__ __forceinline__ void scan_row_general(const Stage &S, const Inst &I, 
 template <bool kBatched>
 __device__ __forceinline__ void init_consume_chunk(const Params &P, const Stage &S, const Inst &I,
                                                    int cc, int lane, int64_t band_lo, int64_t late,
+                                                   unsigned long long *band_cnt,
                                                    unsigned long long &my_pairs) {
     const StageHdr &h = S.h;
     const int32_t n = I.n;
@@ -287,15 +294,22 @@ __device__ __forceinline__ void init_consume_chunk(const Params &P, const Stage 
     const int r = cnt > 1 ? cnt - 1 : 0;
     const int incl = warp_incl_scan(r, lane);
     const int total = __shfl_sync(kFull, incl, 31);
-    const int64_t qbeg = I.q_off + beg;
+    if (total == 0) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(band_cnt, (unsigned long long)total);
+    base = __shfl_sync(kFull, base, 0);
+    if (lane == 0) my_pairs += (unsigned long long)total;
     if (r > 0) {
-        int64_t slot = qbeg + (incl - r);
+        int64_t slot = h.qband + (int64_t)base + (incl - r);
+        if (slot + r > P.q_cap) { raise_err(P.err, kErrIndex); return; }   // corrupt rows only
         if (fast) {
             const int32_t* col = S.ci + (a - h.ci_lo);
             while (resmask) {
                 const int t = __ffs(resmask) - 1;
                 resmask &= resmask - 1;
-                P.q[slot++] = make_int2(i, col[t]);
+                P.q[slot] = make_int2(i, col[t]);
+                if (kBatched) P.qk[slot] = h.k;
+                ++slot;
             }
         } else {
             for (int32_t e = a; e < a_next; ++e) {
@@ -303,18 +317,13 @@ __device__ __forceinline__ void init_consume_chunk(const Params &P, const Stage 
                 const int32_t j = (e >= h.ci_lo && e < h.ci_hi) ? S.ci[e - h.ci_lo] : __ldg(I.col_idx + e);
                 const int64_t we = ge >> 5;
                 const uint32_t w = (we >= h.w_lo && we < h.w_hi) ? S.bw[we - h.w_lo] : __ldg(I.bits + we);
-                if (((w >> (ge & 31)) & 1u) && (uint32_t)j < (uint32_t)i && e != mk)
-                    P.q[slot++] = make_int2(i, j);
+                if (((w >> (ge & 31)) & 1u) && (uint32_t)j < (uint32_t)i && e != mk) {
+                    P.q[slot] = make_int2(i, j);
+                    if (kBatched) P.qk[slot] = h.k;
+                    ++slot;
+                }
             }
         }
-    }
-    if (lane == 0) {
-        ChunkRec rc;
-        rc.qbeg = qbeg;
-        rc.cnt = total;
-        rc.inst = h.k;
-        P.rec[I.chunk_begin + s0 / kChunk] = rc;
-        my_pairs += (unsigned long long)total;
     }
 }
 
@@ -333,6 +342,8 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
         }
         mbar_fence_init();
     }
+    __shared__ unsigned long long band_cnt;
+    if (threadIdx.x == 0) band_cnt = 0;
     __syncthreads();
     if (warp == kInitConsumers) {               // producer warp
         if (lane == 0) init_produce<kBatched>(P, st, full, empty);
@@ -354,12 +365,15 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
         for (int q = 0; q < kChunksPerConsumer; ++q) {
             const int cc = warp * kChunksPerConsumer + q;
             if (cc * kChunk >= S.h.ts) break;
-            init_consume_chunk<kBatched>(P, S, I, cc, lane, band_lo, tile - kStages, my_pairs);
+            init_consume_chunk<kBatched>(P, S, I, cc, lane, band_lo, tile - kStages, &band_cnt, my_pairs);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
     }
-    if (lane == 0 && my_pairs) atomicAdd(P.counters, my_pairs);
+    if (lane == 0 && my_pairs) {
+        atomicAdd(P.counters, my_pairs);
+        atomicAdd(&P.band[blockIdx.x].cnt, my_pairs);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -395,20 +409,25 @@ __global__ void __launch_bounds__(512) k_analysis(Params P) {
                 act[u] = site[u] < I.n;
             }
         }
+        // all loads of a round are issued before any result is used, so the
+        // kAnaChunks chains of a lane are in flight together
+#pragma unroll
+        for (int u = 0; u < kAnaChunks; ++u) x[u] = act[u] ? L[u][site[u]] : 0;
 #pragma unroll
         for (int u = 0; u < kAnaChunks; ++u) {
-            x[u] = act[u] ? L[u][site[u]] : 0;
             first[u] = x[u];
             act[u] = act[u] && x[u] != site[u];
         }
         for (int32_t it = 0;; ++it) {
+            int32_t y[kAnaChunks];
+#pragma unroll
+            for (int u = 0; u < kAnaChunks; ++u) y[u] = act[u] ? L[u][x[u]] : 0;
             bool any = false;
 #pragma unroll
             for (int u = 0; u < kAnaChunks; ++u) {
                 if (act[u]) {
-                    const int32_t y = L[u][x[u]];
-                    if (y == x[u]) act[u] = false;
-                    else { x[u] = y; any = true; }
+                    if (y[u] == x[u]) act[u] = false;
+                    else { x[u] = y[u]; any = true; }
                 }
             }
             if (!any) break;
@@ -422,116 +441,141 @@ __global__ void __launch_bounds__(512) k_analysis(Params P) {
 
 // ---------------------------------------------------------------------------
 // Step (iii): label reduction, Algorithm 1 for every residual pair (i, j).
-// A warp takes 32 chunk records and drains their pairs; a lane that finishes
-// a pair takes the next. For a pair the lane walks both label chains at once
-// (find the roots), points the first nodes of long chains at the root with
-// atomicMin (labels only decrease, so this never undoes a merge), then runs
-// Algorithm 1's atomicMin loop on the two roots.
+// The pairs of all bands form one flat index space (prefix sums of the band
+// counts, in shared memory). A thread carries kRedTasks pairs at once, taken
+// a grid-width apart so that the pair loads coalesce, and advances all of
+// them in lockstep: chase both label chains of a pair to their roots (one
+// load per chain per round), point a start node whose chain was longer than
+// one hop at the root with atomicMin (labels only decrease, so this never
+// undoes a merge), then run Algorithm 1's atomicMin loop on the two roots.
 
-struct RedTask {
-    int32_t *L;
-    int32_t sa, sb, xa, xb, a0, b0, ha, hb, r1, r2, it, cap;
-    bool has, merge, da, db;
-};
+enum : int32_t { kTaskDone = 0, kTaskChase = 1, kTaskRoot = 2, kTaskMerge = 3 };
 
-__device__ __forceinline__ void red_finish_chase(RedTask &t) {
-    // chain sa -> a0 -> ... -> xa: sa is stale if ha >= 2, a0 if ha >= 3
-    if (t.ha >= 2) atomicMin(t.L + t.sa, t.xa);
-    if (t.ha >= 3) atomicMin(t.L + t.a0, t.xa);
-    if (t.hb >= 2) atomicMin(t.L + t.sb, t.xb);
-    if (t.hb >= 3) atomicMin(t.L + t.b0, t.xb);
-    t.r1 = max(t.xa, t.xb);
-    t.r2 = min(t.xa, t.xb);
-    if (t.r1 == t.r2) t.has = false;
-    else { t.merge = true; t.it = 0; }
-}
+// Chase loads may be served from L1: a stale label is an older ancestor,
+// which only lengthens a walk (labels only decrease), and every merge goes
+// through an atomicMin whose returned value is current.
+__device__ __forceinline__ int32_t red_load(const int32_t *p) { return __ldca(p); }
 
 template <bool kBatched>
-__global__ void __launch_bounds__(512) k_reduce(Params P) {
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
+__global__ void __launch_bounds__(256) k_reduce(Params P) {
+    __shared__ long long s_pref[kMaxBands + 1];
+    if (threadIdx.x == 0) {
+        long long acc = 0;
+        for (int b = 0; b < P.n_bands; ++b) {
+            s_pref[b] = acc;
+            acc += (long long)P.band[b].cnt;
+        }
+        s_pref[P.n_bands] = acc;
+    }
+    __syncthreads();
+    const long long total = s_pref[P.n_bands];
+    const long long T = (long long)gridDim.x * blockDim.x;
 #ifdef CCL_DEVICE_STATS
     unsigned long long st_hops = 0, st_atom = 0, st_iter = 0;
 #endif
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t ngroups = (P.n_chunks + 31) / 32;
-    for (int64_t gidx = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); gidx < ngroups;
-         gidx += nwarps) {
-        const int64_t c = gidx * 32 + lane;
-        ChunkRec rc;
-        if (c < P.n_chunks) rc = P.rec[c]; else { rc.qbeg = 0; rc.cnt = 0; rc.inst = 0; }
-        const int incl = warp_incl_scan(rc.cnt, lane);
-        const int excl = incl - rc.cnt;
-        const int total = __shfl_sync(kFull, incl, 31);
-        if (total == 0) continue;
-        int next = 0;
-        RedTask t;
-        t.has = false;
-        for (;;) {
-            // refill
-            const unsigned need = __ballot_sync(kFull, !t.has);
-            const int p = next + __popc(need & lt);
-            int src = 0;
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    // a thread's kRedTasks pairs are consecutive queue entries (neighbouring
+    // sites, so their chains overlap in cache)
+    for (long long base = gtid * kRedTasks; base < total; base += (long long)kRedTasks * T) {
+        // task u: phase st, nodes a > b (chase: current nodes of the two
+        // chains; root: a = root of one tree, b walking to the other root;
+        // merge: Algorithm 1's label_1 = a, label_2 = b)
+        int32_t *L[kRedTasks];
+        int32_t cap[kRedTasks], a[kRedTasks], b[kRedTasks], it[kRedTasks], st[kRedTasks];
 #pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const int cand = src + step;
-                const int ex = __shfl_sync(kFull, excl, cand);
-                if (ex <= p) src = cand;
-            }
-            const long long qb = __shfl_sync(kFull, (long long)rc.qbeg, src);
-            const int ex_src = __shfl_sync(kFull, excl, src);
-            const int kk = __shfl_sync(kFull, rc.inst, src);
-            if (!t.has && p < total) {
-                const int2 pr = P.q[qb + (p - ex_src)];
-                if (kBatched) {
-                    t.L = P.insts[kk].labels;
-                    t.cap = P.insts[kk].n;
-                } else {
-                    t.L = P.one.labels;
-                    t.cap = P.one.n;
+        for (int u = 0; u < kRedTasks; ++u) {
+            const long long p = base + u;
+            st[u] = kTaskDone;
+            L[u] = P.one.labels;
+            cap[u] = P.one.n;
+            a[u] = b[u] = 0;
+            it[u] = 0;
+            if (p < total) {
+                int lo = 0, hi = P.n_bands - 1;       // band of pair p
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_pref[mid] <= p) lo = mid; else hi = mid - 1;
                 }
-                t.sa = t.xa = pr.x;
-                t.sb = t.xb = pr.y;
-                t.ha = t.hb = 0;
-                t.da = t.db = false;
-                t.merge = false;
-                t.has = true;
+                const long long slot = P.band[lo].qbase + (p - s_pref[lo]);
+                const int2 pr = P.q[slot];
+                if (kBatched) {
+                    const int k = P.qk[slot];
+                    L[u] = P.insts[k].labels;
+                    cap[u] = P.insts[k].n;
+                }
+                a[u] = max(pr.x, pr.y);
+                b[u] = min(pr.x, pr.y);
+                st[u] = kTaskChase;
             }
-            next = min(next + __popc(need), total);
-            // one step
+        }
+        for (;;) {
 #ifdef CCL_DEVICE_STATS
             st_iter++;
-            if (t.has) { if (t.merge) st_atom++; else st_hops += (!t.da) + (!t.db); }
 #endif
-            if (t.has) {
-                if (!t.merge) {
-                    if (!t.da) {
-                        const int32_t y = __ldcg(t.L + t.xa);
-                        if (y == t.xa) t.da = true;
-                        else { if (t.ha == 0) t.a0 = y; t.xa = y; ++t.ha; }
-                    }
-                    if (!t.db) {
-                        const int32_t y = __ldcg(t.L + t.xb);
-                        if (y == t.xb) t.db = true;
-                        else { if (t.hb == 0) t.b0 = y; t.xb = y; ++t.hb; }
-                    }
-                    if (t.ha > t.cap || t.hb > t.cap) { raise_err(P.err, kErrNonconv); t.has = false; }
-                    else if (t.da && t.db) red_finish_chase(t);
-                } else {
-                    const int32_t old = atomicMin(t.L + t.r1, t.r2);
-                    if (old == t.r2 || old == t.r1) t.has = false;
-                    else if (old > t.r2) t.r1 = old;
-                    else { t.r1 = t.r2; t.r2 = old; }
-                    if (++t.it > 2 * t.cap + 4) { raise_err(P.err, kErrNonconv); t.has = false; }
-                }
+            // issue: one load or one atomicMin per live task
+            int32_t v[kRedTasks];
+#pragma unroll
+            for (int u = 0; u < kRedTasks; ++u) {
+                if (st[u] == kTaskChase) v[u] = red_load(L[u] + a[u]);
+                else if (st[u] == kTaskRoot) v[u] = red_load(L[u] + b[u]);
+                else if (st[u] == kTaskMerge) v[u] = atomicMin(L[u] + a[u], b[u]);
+                else v[u] = 0;
             }
-            if (!__any_sync(kFull, t.has) && next >= total) break;
+            // use
+            bool any = false;
+#pragma unroll
+            for (int u = 0; u < kRedTasks; ++u) {
+                if (st[u] == kTaskChase) {
+                    // Root finding of Algorithm 1 for both ends at once. Labels
+                    // decrease towards a root, so the larger current node a
+                    // cannot be an ancestor of b: it is the one advanced.
+                    // Meeting means one tree (label_1 == label_2, nothing to
+                    // do); a root at a means two trees.
+#ifdef CCL_DEVICE_STATS
+                    st_hops++;
+#endif
+                    const int32_t y = v[u];
+                    if (y == a[u]) {
+                        // a is a root: Algorithm 1 links it under b's root
+                        // (link mode 0); link mode 1 links it under b itself,
+                        // which skips the walk to b's root
+                        st[u] = P.link_mode ? kTaskMerge : kTaskRoot;
+                        it[u] = 0;
+                    } else if (y == b[u]) {
+                        st[u] = kTaskDone;
+                    } else {
+                        a[u] = max(y, b[u]);
+                        b[u] = min(y, b[u]);
+                    }
+                } else if (st[u] == kTaskRoot) {
+#ifdef CCL_DEVICE_STATS
+                    st_hops++;
+#endif
+                    if (v[u] == b[u]) st[u] = kTaskMerge;
+                    else b[u] = v[u];
+                } else if (st[u] == kTaskMerge) {
+#ifdef CCL_DEVICE_STATS
+                    st_atom++;
+#endif
+                    // Algorithm 1's atomicMin outcome on label_1 = a, label_2 = b
+                    const int32_t old = v[u];
+                    if (old == b[u] || old == a[u]) st[u] = kTaskDone;
+                    else if (old > b[u]) a[u] = old;
+                    else { a[u] = b[u]; b[u] = old; }
+                }
+                if (st[u] != kTaskDone && ++it[u] > 4 * cap[u] + 8) {
+                    raise_err(P.err, kErrNonconv);
+                    st[u] = kTaskDone;
+                }
+                any |= st[u] != kTaskDone;
+            }
+            if (!any) break;
         }
     }
 #ifdef CCL_DEVICE_STATS
     if (st_hops) atomicAdd(P.counters + 1, st_hops);
     if (st_atom) atomicAdd(P.counters + 2, st_atom);
-    if (lane == 0 && st_iter) atomicAdd(P.counters + 3, st_iter);
+    if (st_iter) atomicAdd(P.counters + 3, st_iter);
 #endif
 }
 

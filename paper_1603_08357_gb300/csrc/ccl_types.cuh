@@ -24,7 +24,11 @@ constexpr int kBitBuf = kColCap / 32 + 12;
 constexpr int kRowRegs = 8;                // rows up to this degree are scanned in registers
 
 // steps (ii)/(iv): chunks a warp walks at once
-constexpr int kAnaChunks = 2;
+constexpr int kAnaChunks = 4;
+
+// step (iii): pairs a thread carries at once; most step-(i) CTAs (bands)
+constexpr int kRedTasks = 4;
+constexpr int kMaxBands = 1024;
 
 // latched device error bits
 constexpr unsigned kErrIndex = 1u;         // col_idx or row_ptr out of range
@@ -49,22 +53,26 @@ struct Inst {
     int32_t nnz;
 };
 
-// Per-chunk record written by step (i) and read by step (iii).
-struct __align__(16) ChunkRec {
-    int64_t qbeg;              // first queue slot of the chunk's pairs
-    int32_t cnt;               // residual pairs of the chunk
-    int32_t inst;              // instance of the chunk
+// Residual pairs of one step-(i) CTA: they are packed from queue slot qbase
+// on (inside the slot range of the band's CSR entries, so bands never overlap).
+struct __align__(16) BandRec {
+    int64_t qbase;
+    unsigned long long cnt;
 };
 
 struct Params {
     const Inst *insts;         // device table, K entries (K > 1)
     Inst one;                  // the instance when K == 1
     int32_t K;
-    int32_t dedup;
+    int32_t link_mode;         // step (iii): 0 root to root, 1 root to the other chain's node
     int64_t n_chunks;          // over all instances
     int64_t n_tiles;           // over all instances
-    ChunkRec *rec;             // [n_chunks]
-    int2 *q;                   // residual pairs (i, j), slots indexed by global entry
+    int32_t n_bands;           // CTAs of step (i)
+    int32_t pad_;
+    BandRec *band;             // [n_bands]
+    int2 *q;                   // residual pairs (i, j); slots indexed by global CSR entry
+    int32_t *qk;               // instance of each pair (K > 1 only)
+    int64_t q_cap;             // slots of q (and qk)
     unsigned *err;
     unsigned long long *counters;   // [0] residual pairs
 };
@@ -76,7 +84,8 @@ struct __align__(16) StageHdr {
     int32_t rp_lo, rp_hi;      // row pointers present (indices relative to Inst::row_ptr)
     int32_t ci_lo, ci_hi;      // column entries present (relative to Inst::col_idx)
     int32_t status;            // 0 valid, 1 corrupt row pointers
-    int32_t pad_[3];
+    int32_t pad_;
+    int64_t qband;             // first queue slot of this CTA's band
 };
 
 struct __align__(16) Stage {

@@ -95,12 +95,12 @@ def test_standard_bethe_has_no_residual_pairs(ctx, z, S):
 
 @pytest.mark.parametrize("threads", [64, 128, 256, 512])
 @pytest.mark.parametrize("pre", [0, 1])
-@pytest.mark.parametrize("dedup", [0, 1])
-def test_launch_options_same_labels(threads, pre, dedup):
+@pytest.mark.parametrize("link", [0, 1])
+def test_launch_options_same_labels(threads, pre, link):
     c = ccl.ccl_context_create(0)
     try:
         for opt, val in ((ccl.CCL_OPT_BLOCK_THREADS, threads), (ccl.CCL_OPT_PRE_ANALYSIS, pre),
-                         (ccl.CCL_OPT_DEDUP, dedup), (ccl.CCL_OPT_CTAS_PER_SM, 1 if threads == 64 else 0)):
+                         (ccl.CCL_OPT_LINK_MODE, link), (ccl.CCL_OPT_CTAS_PER_SM, 1 if threads == 64 else 0)):
             assert ccl.ccl_set_option(c, opt, val) == ccl.CCL_OK
         lat = L.triangle(300, 0.52, 11)
         want = oracle.uf_label(lat)
