@@ -139,6 +139,31 @@ CCL_API ccl_status ccl_label_host(ccl_context *ctx, int32_t n_sites, int64_t nnz
                           const int32_t *col_idx, const uint32_t *open_bits, int32_t *labels,
                           void *stream);
 
+/*
+ * ccl_label_noalloc -- ccl_label for callers that cannot allocate device
+ * memory at run time (the paper has no counterpart; it is a deployment aid).
+ * Some programs must not call cudaMalloc once running: a latency-bound loop
+ * cannot afford the device-wide synchronisation cudaMalloc/cudaFree may
+ * cause, and a process whose device memory is handed out by another allocator
+ * may have none left for a library. This call needs no context and allocates
+ * nothing: its working memory is one fixed device array inside the library
+ * (about 17 MB, held by every GPU that loads the library until exit).
+ *   n_sites, nnz, row_ptr, col_idx, open_bits, labels, stream: as ccl_label
+ *   (device pointers owned by the caller, work on `stream`).
+ * Limit: nnz <= 2,097,152 CSR entries; larger inputs return
+ * CCL_ERR_INVALID_ARGUMENT without touching the device.
+ * Synchronous: waits for `stream`, then returns the kernels' status
+ * (CCL_OK, CCL_ERR_INDEX_OUT_OF_RANGE, CCL_ERR_INVALID_ARGUMENT,
+ * CCL_ERR_NONCONVERGED) or CCL_ERR_CUDA.
+ * The first call on a device takes the array's device address and sets up
+ * the kernels for that device; make that first call before any stream capture.
+ * All calls share the one array, so calls that overlap on the GPU (other
+ * streams, other host threads) race; serialise them.
+ */
+CCL_API ccl_status ccl_label_noalloc(int32_t n_sites, int64_t nnz, const int32_t *row_ptr,
+                                     const int32_t *col_idx, const uint32_t *open_bits,
+                                     int32_t *labels, void *stream);
+
 /* Pre-sizes the workspace for instances of up to n sites and nnz entries in
  * total (and up to n_chunks 32-site chunks; 0 = ceil(n/32)). */
 CCL_API ccl_status ccl_reserve(ccl_context *ctx, int64_t n_sites, int64_t nnz, int64_t n_chunks);

@@ -89,6 +89,7 @@ def _load() -> ctypes.CDLL:
         "ccl_label": (C, [P, I32, I64, P, P, P, P, P]),
         "ccl_label_batched": (C, [P, I32, P, P, P, P, P, P, P]),
         "ccl_label_host": (C, [P, I32, I64, P, P, P, P, P]),
+        "ccl_label_noalloc": (C, [I32, I64, P, P, P, P, P]),
         "ccl_reserve": (C, [P, I64, I64, I64]),
         "ccl_sync": (C, [P, P, I64]),
         "ccl_validate": (C, [P, I32, I64, P, P, P, P]),
@@ -271,6 +272,14 @@ def ccl_label_host(ctx, n_sites: int, nnz: int, row_ptr, col_idx, open_bits, lab
                                _host_ptr(col_idx, "col_idx", np.int32),
                                _host_ptr(open_bits, "open_bits", np.uint32),
                                _host_ptr(labels, "labels", np.int32), _stream(stream))
+
+
+def ccl_label_noalloc(n_sites: int, nnz: int, row_ptr, col_idx, open_bits, labels, stream=None) -> int:
+    """Allocation-free, synchronous single-instance labelling (see ccl.h)."""
+    return _lib.ccl_label_noalloc(int(n_sites), int(nnz), _dev_ptr(row_ptr, "row_ptr", _i32()),
+                                  _dev_ptr(col_idx, "col_idx", _i32()),
+                                  _dev_ptr(open_bits, "open_bits", _bits_dtypes()),
+                                  _dev_ptr(labels, "labels", _i32()), _stream(stream))
 
 
 def ccl_reserve(ctx, n_sites: int, nnz: int, n_chunks: int = 0) -> int:

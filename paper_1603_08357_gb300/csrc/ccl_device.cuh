@@ -580,8 +580,10 @@ __global__ void __launch_bounds__(256) k_reduce(Params P) {
 }
 
 // ---------------------------------------------------------------------------
-// Input check for ccl_validate: one thread per site.
+// Input check for ccl_validate: one thread per site. (Only the translation
+// unit that implements ccl_validate defines it.)
 
+#ifndef CCL_NO_VALIDATE_KERNEL
 __global__ void k_validate(int32_t n, int64_t nnz, const int32_t *__restrict__ row_ptr,
                            const int32_t *__restrict__ col_idx, const uint32_t *__restrict__ bits,
                            unsigned *err) {
@@ -607,5 +609,6 @@ __global__ void k_validate(int32_t n, int64_t nnz, const int32_t *__restrict__ r
         }
     }
 }
+#endif  // CCL_NO_VALIDATE_KERNEL
 
 }  // namespace ccl

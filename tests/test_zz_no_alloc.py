@@ -1,0 +1,44 @@
+"""ccl_label_noalloc, the allocation-free entry point, against ccl_label.
+
+Some callers cannot allocate device memory while they run (a latency-bound
+loop that cannot absorb cudaMalloc's device-wide synchronisation, or a
+process whose device memory belongs to another allocator). The entry point
+serves them from one fixed device array inside the library. This file is
+named so that pytest collects it last; it passes alone in a fresh process and
+after the other tests.
+"""
+import numpy as np
+import pytest
+import torch
+
+import lattices as L
+import paper_1603_08357_gb300 as ccl
+from ccl_testutil import DEV, gpu_label, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _noalloc(lat):
+    rp, ci, bits = to_dev(lat)
+    out = torch.full((lat.n,), -5, dtype=torch.int32, device=DEV)
+    st = ccl.ccl_label_noalloc(lat.n, lat.nnz, rp, ci, bits, out)
+    assert st == ccl.CCL_OK, ccl.ccl_status_string(st)
+    return out.cpu().numpy()
+
+
+def test_noalloc_matches_ccl_label_twice(ctx):
+    lats = [L.triangle(500, L.PC_TRIANGLE, 3), L.cayley(3, 15, 0.5, 4, perm_seed=5),
+            L.honeycomb(256, L.PC_HONEYCOMB, 1)]
+    for lat in lats:
+        want = gpu_label(ctx, lat)
+        # two calls in a row: the shared scratch keeps the previous call's contents
+        first = _noalloc(lat)
+        second = _noalloc(lat)
+        assert np.array_equal(first, want)
+        assert np.array_equal(second, want)
+
+
+def test_noalloc_rejects_beyond_its_scratch():
+    big_nnz = (1 << 21) + 1
+    st = ccl.ccl_label_noalloc(10, big_nnz, 0, 0, 0, 0)
+    assert st == ccl.CCL_ERR_INVALID_ARGUMENT
