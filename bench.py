@@ -137,13 +137,30 @@ def oracle_time(lat, budget_s: float, min_reps: int = 1):
     return lat.n * reps / el, reps, el
 
 
-def make_workload(name: str, rank: int):
+def replica_spec(name: str, rank: int) -> dict:
+    """The instance rank `rank` labels: the workload with its seeds offset per
+    rank (replicas: every rank labels an independent instance of the same
+    shape; nothing is exchanged)."""
     c = dict(CONFIGS[name])
-    desc = c.pop("desc")
-    c["seed"] = c["seed"] + 1000 * rank      # replicas: one seeded instance per rank
+    c.pop("desc")
+    c["seed"] = c["seed"] + 1000 * rank
     if "perm_seed" in c:
         c["perm_seed"] = c["perm_seed"] + 1000 * rank
-    return L.make_instance(c), desc
+    return c
+
+
+def make_workload(name: str, rank: int):
+    return L.make_instance(replica_spec(name, rank)), CONFIGS[name]["desc"]
+
+
+def max_over_ranks(value: float, dist, device=None) -> float:
+    """The job's step time: the slowest rank's (barrier-bracketed) time."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def algorithmic_bytes(n: int, nnz: int, q: int) -> dict:
@@ -289,12 +306,7 @@ def run_ours(args, rank, world, local):
     ms_local = sum(step_ms) / args.steps
     kern = ccl.ccl_get_step_times(ctx)
     ccl.ccl_set_option(ctx, ccl.CCL_OPT_PROFILE, 0)
-    if dist:
-        t = torch.tensor([ms_local], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    else:
-        ms = ms_local
+    ms = max_over_ranks(ms_local, dist, dev)
 
     # graph-replay steps (the production path) for comparison
     for _ in range(3):
@@ -328,11 +340,7 @@ def run_ours(args, rank, world, local):
     t0 = time.perf_counter()
     for _ in range(e_steps):
         e2e_step()
-    e_ms = 1e3 * (time.perf_counter() - t0) / e_steps
-    if dist:
-        t = torch.tensor([e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_ms = float(t.item())
+    e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / e_steps, dist, dev)
 
     # sampled parity guard on the labels of the last step
     import oracle
@@ -391,13 +399,140 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def run_batched(args, rank, world, local):
+    """The batched workload: K mixed instances labelled by one pass of the four
+    steps (ccl_label_batched, graph replay), against the same instances
+    labelled one ccl_label call at a time."""
+    import torch
+    import oracle
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1603_08357_gb300 as ccl
+    t_gen = time.perf_counter()
+    specs = L.batched_mix_specs(args.instances, seed=4 + 1000 * rank)
+    b = L.make_batch(specs)
+    abits, word_off = b.aligned_bits()
+    t_gen = time.perf_counter() - t_gen
+    rp = torch.from_numpy(b.row_ptr).to(dev)
+    ci = torch.from_numpy(b.col_idx).to(dev)
+    bits = torch.from_numpy(b.open_bits.view(np.int32)).to(dev)
+    abits_d = torch.from_numpy(abits.view(np.int32)).to(dev)
+    labels = torch.empty(b.n_total, dtype=torch.int32, device=dev)
+    ctx = ccl.ccl_context_create(local)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        st = ccl.ccl_label_batched(ctx, b.k, b.site_off, b.ent_off, rp, ci, bits, labels, stream)
+        if st != ccl.CCL_OK:
+            raise ccl.CclError(st, "ccl_label_batched")
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    ccl.check(ccl.ccl_sync(ctx, stream), "warm-up")
+    q = int(ccl.ccl_get_stats(ctx).residual_pairs)
+    clocks = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    torch.cuda.nvtx.range_push("timed")
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ccl.check(ccl.ccl_sync(ctx, stream), "timed steps")
+    ms = max_over_ranks(sum(a.elapsed_time(c) for a, c in ev) / args.steps, dist, dev)
+    got = labels.cpu().numpy()
+
+    # one instance per call (graphs off: every instance is a new shape)
+    one = ccl.ccl_context_create(local)
+    ccl.ccl_set_option(one, ccl.CCL_OPT_USE_GRAPHS, 0)
+    out1 = torch.empty_like(labels)
+    rp0, ci0, ab0, lab0 = rp.data_ptr(), ci.data_ptr(), abits_d.data_ptr(), out1.data_ptr()
+    so, eo = b.site_off, b.ent_off
+
+    def one_step():
+        for k in range(b.k):
+            n_k, nnz_k = int(so[k + 1] - so[k]), int(eo[k + 1] - eo[k])
+            st = ccl.ccl_label(one, n_k, nnz_k, rp0 + 4 * (int(so[k]) + k), ci0 + 4 * int(eo[k]),
+                               ab0 + 4 * int(word_off[k]), lab0 + 4 * int(so[k]), stream)
+            if st != ccl.CCL_OK:
+                raise ccl.CclError(st, "ccl_label")
+
+    one_step()
+    ccl.check(ccl.ccl_sync(one, stream), "one-at-a-time warm-up")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(1, min(args.steps, 3))
+    e0.record(stream)
+    for _ in range(reps):
+        one_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_one = max_over_ranks(e0.elapsed_time(e1) / reps, dist, dev)
+    same = bool(torch.equal(out1, labels))
+
+    # parity: a seeded sample of instances against the oracle
+    rng = np.random.default_rng(11 + rank)
+    sample = sorted(rng.choice(b.k, size=min(args.parity_sample, b.k), replace=False).tolist())
+    ok = True
+    for k in sample:
+        s0, s1 = int(so[k]), int(so[k + 1])
+        if not np.array_equal(got[s0:s1], oracle.uf_label(b.instance(k))):
+            ok = False
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            t0, done, sites = time.perf_counter(), 0, 0
+            for k in sample:
+                oracle.uf_label(b.instance(k))
+                sites += int(so[k + 1] - so[k])
+                done += 1
+                if time.perf_counter() - t0 > args.cpu_seconds:
+                    break
+            el = time.perf_counter() - t0
+            cpu = {"value": sites / el, "unit": "sites/s", "cores": 1, "kind": "oracle",
+                   "sample": f"union-find oracle over {done} instances of the batch ({sites} sites), 1 thread"}
+        line = {
+            "metric": "sites labeled/s (batched)", "value": world * b.n_total / (ms / 1e3), "unit": "sites/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": "batched", "instances": b.k, "n_sites": b.n_total, "nnz": b.nnz_total,
+                       "residual_pairs": q, "generation_s": t_gen,
+                       "l2": "inputs larger than L2 (no flush)"},
+            "one_at_a_time": {"ms_per_step": ms_one, "value": world * b.n_total / (ms_one / 1e3),
+                              "calls_per_step": b.k, "speedup_batched": ms_one / ms,
+                              "labels_identical": same},
+            "path_alg_gbs": algorithmic_bytes(b.n_total, b.nnz_total, q)["path"] / (ms / 1e3) / 1e9,
+            "cpu_baseline": cpu,
+            "gpu_launches": args.steps * 4,
+            "clocks": clk,
+            "parity_sample": {"instances": len(sample), "ok": ok},
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=sorted(CONFIGS), default="tri4096")
+    ap.add_argument("--config", choices=sorted(CONFIGS) + ["batched"], default="tri4096")
+    ap.add_argument("--instances", type=int, default=4096)
+    ap.add_argument("--parity-sample", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-autotune", action="store_true")
@@ -405,6 +540,8 @@ def main():
     rank, world, local = _env_rank()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.config == "batched":
+        run_batched(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
 

@@ -72,6 +72,9 @@ def _load():
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                      ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
                                      ctypes.POINTER(ctypes.c_int64)]
+            lib.lat_copy_bits.restype = None
+            lib.lat_copy_bits.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.c_void_p, ctypes.c_int64]
             lib.lat_permutation.restype = None
             lib.lat_permutation.argtypes = [ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p,
                                             ctypes.c_void_p]
@@ -285,6 +288,23 @@ class Batch:
     @property
     def nnz_total(self) -> int:
         return int(self.ent_off[-1])
+
+    def aligned_bits(self, nthreads=None):
+        """The bits again, each instance starting on a word boundary: returns
+        (bits, word_off) with instance k's entry e at bit 32*word_off[k] + e."""
+        nnz = np.diff(self.ent_off)
+        words = (nnz + 31) // 32
+        word_off = np.zeros(self.k + 1, np.int64)
+        word_off[1:] = np.cumsum(words)
+        out = np.zeros(max(1, int(word_off[-1])), np.uint32)
+        lib = _load()
+
+        def one(k):
+            lib.lat_copy_bits(self.open_bits.ctypes.data, int(self.ent_off[k]), int(nnz[k]),
+                              out.ctypes.data, 32 * int(word_off[k]))
+        with ThreadPoolExecutor(max_workers=nthreads or _threads()) as ex:
+            list(ex.map(one, range(self.k)))
+        return out, word_off
 
     def instance(self, k: int) -> Lattice:
         s0, s1 = int(self.site_off[k]), int(self.site_off[k + 1])

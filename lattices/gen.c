@@ -274,6 +274,18 @@ int64_t lat_fill(const lat_desc *d, uint64_t seed, double p,
     return acc;
 }
 
+/* Copies n_bits bits from bit position src_off of src to bit position dst_off
+ * of dst (dst words outside the copied range keep their other bits). */
+void lat_copy_bits(const uint32_t *src, int64_t src_off, int64_t n_bits, uint32_t *dst,
+                   int64_t dst_off) {
+    for (int64_t t = 0; t < n_bits; ++t) {
+        const int64_t gs = src_off + t, gd = dst_off + t;
+        const uint32_t bit = (src[gs >> 5] >> (gs & 31)) & 1u;
+        if (bit) dst[gd >> 5] |= 1u << (gd & 31);
+        else dst[gd >> 5] &= ~(1u << (gd & 31));
+    }
+}
+
 /* Seeded uniform permutation by Fisher-Yates; the swap index for position i
  * (i = n-1 .. 1) is floor(out * (i+1) / 2^64) with out = SplitMix64 output
  * number n-1-i from `seed`. perm[s] = stored index of standard site s. */

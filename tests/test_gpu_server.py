@@ -1,0 +1,104 @@
+"""The request loop (continuous batching): requests submitted while others are
+on the GPU are admitted as memory frees up, batched and labelled; every result
+must equal the oracle's and the result of the same request labelled alone."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import lattices as L
+import oracle
+import paper_1603_08357_gb300 as ccl
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests(count, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for r in range(count):
+        t = int(rng.integers(0, 3))
+        if t == 0:
+            lat = L.honeycomb(int(rng.integers(2, 90)), L.PC_HONEYCOMB, 100 + r)
+        elif t == 1:
+            lat = L.triangle(int(rng.integers(2, 120)), L.PC_TRIANGLE, 100 + r)
+        else:
+            lat = L.cayley(3, int(rng.integers(1, 12)), 0.5, 100 + r, perm_seed=r)
+        out.append(lat)
+    return out
+
+
+def _submit(srv, lat):
+    st, ticket = ccl.ccl_server_submit(srv, lat.n, lat.nnz, lat.row_ptr, lat.col_idx, lat.open_bits)
+    assert st == ccl.CCL_OK, ccl.ccl_status_string(st)
+    return ticket
+
+
+def _wait(srv, ticket, n):
+    out = np.full(n, -1, np.int32)
+    st = ccl.ccl_server_wait(srv, ticket, out, 60_000)
+    assert st == ccl.CCL_OK, ccl.ccl_status_string(st)
+    return out
+
+
+def test_mixed_stream_matches_alone_and_oracle():
+    reqs = _requests(300, 7)
+    srv = ccl.ccl_server_create(0, n_streams=3, max_batch=64)
+    try:
+        # alone: one request in flight at a time
+        alone = [_wait(srv, _submit(srv, lat), lat.n) for lat in reqs[:40]]
+        # in the mix: everything submitted from two threads, then collected
+        tickets = [None] * len(reqs)
+
+        def feed(idx):
+            for k in idx:
+                tickets[k] = _submit(srv, reqs[k])
+                time.sleep(0.0002)
+        th = [threading.Thread(target=feed, args=(range(s, len(reqs), 2),)) for s in (0, 1)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        mixed = [_wait(srv, tickets[k], reqs[k].n) for k in range(len(reqs))]
+        stats = ccl.ccl_server_stats_get(srv)
+    finally:
+        srv.close()
+    for k, lat in enumerate(reqs):
+        want = oracle.uf_label(lat)
+        assert np.array_equal(mixed[k], want), k
+        if k < len(alone):
+            assert np.array_equal(alone[k], mixed[k])
+    assert stats.completed == 340 and stats.rejected == 0
+    assert stats.batches < stats.completed          # requests were batched together
+    assert 0 < stats.p50_ms <= stats.p99_ms <= stats.max_ms
+
+
+def test_rejection_and_unknown_ticket():
+    srv = ccl.ccl_server_create(0, n_streams=1, hbm_budget=1 << 20)
+    try:
+        big = L.triangle(400, 0.3, 1)                      # needs more than 1 MiB on the device
+        st, _ = ccl.ccl_server_submit(srv, big.n, big.nnz, big.row_ptr, big.col_idx, big.open_bits)
+        assert st == ccl.CCL_ERR_REJECTED
+        small = L.triangle(8, 0.5, 2)
+        t = _submit(srv, small)
+        assert np.array_equal(_wait(srv, t, small.n), oracle.uf_label(small))
+        assert ccl.ccl_server_wait(srv, 987654, None, 10) == ccl.CCL_ERR_NOT_FOUND
+        assert ccl.ccl_server_stats_get(srv).rejected == 1
+    finally:
+        srv.close()
+
+
+def test_admission_waits_for_memory():
+    """A budget that holds only a few requests at a time: later requests wait
+    for earlier ones to finish, and all complete correctly."""
+    reqs = [L.triangle(150, L.PC_TRIANGLE, s) for s in range(24)]
+    one = 4 * (reqs[0].n + 1) + 4 * reqs[0].nnz + 8 * reqs[0].nnz + 4 * reqs[0].n
+    srv = ccl.ccl_server_create(0, n_streams=2, hbm_budget=3 * one)
+    try:
+        tickets = [_submit(srv, lat) for lat in reqs]
+        outs = [_wait(srv, t, lat.n) for t, lat in zip(tickets, reqs)]
+    finally:
+        srv.close()
+    for lat, got in zip(reqs, outs):
+        assert np.array_equal(got, oracle.uf_label(lat))
