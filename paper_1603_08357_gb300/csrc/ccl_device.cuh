@@ -215,14 +215,24 @@ __device__ __forceinline__ void scan_row_general(const Stage &S, const Inst &I, 
     }
 }
 
-// One chunk of 32 sites. `late` = the last tile of this CTA's band whose
-// labels are final and visible here (tiles at least kStages back), `band_lo`
-// = the band's first tile: a site whose smallest open lower neighbour m lies
-// in a tile in [band_lo, late] takes label[m] (the root of m's tree after
-// steps (i)/(ii)) instead of m, which shortcuts the chain step (ii) would walk.
+// Per-tile values a consumer warp computes once: the stage-relative bit
+// offset of entry 0 and the number of copied bits (32-bit), and the range of
+// the instance's tiles whose labels are final and visible here.
+struct TileCtx {
+    int32_t rb0;        // stage-relative bit index of local entry 0
+    int32_t nbits;      // bits present in the stage
+    int32_t vis_lo;     // instance-local tiles [vis_lo, vis_hi] are visible
+    int32_t vis_hi;
+};
+
+// One chunk of 32 sites. The tiles of this CTA's band that were finished at
+// least kStages tiles ago are visible (their labels were released through the
+// stage barriers): a site whose smallest open lower neighbour m lies in such
+// a tile takes label[m] (the root of m's tree after steps (i)/(ii)) instead of
+// m, which shortcuts the chain step (ii) would walk.
 template <bool kBatched>
 __device__ __forceinline__ void init_consume_chunk(const Params &P, const Stage &S, const Inst &I,
-                                                   int cc, int lane, int64_t band_lo, int64_t late,
+                                                   int cc, int lane, const TileCtx &tc,
                                                    unsigned long long *band_cnt,
                                                    unsigned long long &my_pairs) {
     const StageHdr &h = S.h;
@@ -250,9 +260,8 @@ __device__ __forceinline__ void init_consume_chunk(const Params &P, const Stage 
     const int32_t end = __shfl_sync(kFull, a_next, 31);
     const int32_t deg = a_next - a;
     const int32_t dmax = __reduce_max_sync(kFull, (uint32_t)deg);
-    const int64_t rb0 = I.bit_off - (h.w_lo << 5);      // stage-relative bit of entry 0
-    const bool fast = dmax <= kRowRegs && beg >= h.ci_lo && end <= h.ci_hi && rb0 + beg >= 0 &&
-                      rb0 + end <= 32 * (h.w_hi - h.w_lo);
+    const bool fast = dmax <= kRowRegs && beg >= h.ci_lo && end <= h.ci_hi && tc.rb0 + beg >= 0 &&
+                      tc.rb0 + end <= tc.nbits;
     int32_t m = INT32_MAX, cnt = 0;
     int32_t mk = -1;
     uint32_t resmask = 0;
@@ -261,7 +270,7 @@ __device__ __forceinline__ void init_consume_chunk(const Params &P, const Stage 
         const int32_t* col = S.ci + (a - h.ci_lo);
         uint32_t win = 0;
         if (deg > 0) {
-            const int32_t rel = (int32_t)(rb0 + a);
+            const int32_t rel = tc.rb0 + a;
             win = __funnelshift_r(S.bw[rel >> 5], S.bw[(rel + deg - 1) >> 5], (uint32_t)rel & 31u);
         }
         uint32_t lowmask = 0, jmax = 0;
@@ -286,8 +295,8 @@ __device__ __forceinline__ void init_consume_chunk(const Params &P, const Stage 
     if (bad) raise_err(P.err, kErrIndex);
     int32_t lab = cnt ? m : i;
     if (cnt) {
-        const int64_t mt = I.tile_begin + m / kTileSites;
-        if (mt >= band_lo && mt <= late) lab = __ldcg(I.labels + m);
+        const int32_t mt = m / kTileSites;
+        if (mt >= tc.vis_lo && mt <= tc.vis_hi) lab = __ldcg(I.labels + m);
     }
     if (i < n) I.labels[i] = lab;
 
@@ -361,11 +370,20 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
         }
         const Stage &S = st[s];
         const Inst I = inst_of<kBatched>(P, S.h.k);
+        TileCtx tc;
+        tc.rb0 = (int32_t)(I.bit_off - (S.h.w_lo << 5));
+        tc.nbits = (int32_t)(32 * (S.h.w_hi - S.h.w_lo));
+        {
+            const int64_t lo = max(band_lo, I.tile_begin) - I.tile_begin;
+            const int64_t hi = tile - kStages - I.tile_begin;
+            tc.vis_lo = (int32_t)lo;
+            tc.vis_hi = hi < lo ? -1 : (int32_t)hi;
+        }
 #pragma unroll 1
         for (int q = 0; q < kChunksPerConsumer; ++q) {
             const int cc = warp * kChunksPerConsumer + q;
             if (cc * kChunk >= S.h.ts) break;
-            init_consume_chunk<kBatched>(P, S, I, cc, lane, band_lo, tile - kStages, &band_cnt, my_pairs);
+            init_consume_chunk<kBatched>(P, S, I, cc, lane, tc, &band_cnt, my_pairs);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
@@ -442,12 +460,19 @@ __global__ void __launch_bounds__(512) k_analysis(Params P) {
 // ---------------------------------------------------------------------------
 // Step (iii): label reduction, Algorithm 1 for every residual pair (i, j).
 // The pairs of all bands form one flat index space (prefix sums of the band
-// counts, in shared memory). A thread carries kRedTasks pairs at once, taken
-// a grid-width apart so that the pair loads coalesce, and advances all of
-// them in lockstep: chase both label chains of a pair to their roots (one
-// load per chain per round), point a start node whose chain was longer than
-// one hop at the root with atomicMin (labels only decrease, so this never
-// undoes a merge), then run Algorithm 1's atomicMin loop on the two roots.
+// counts, in shared memory). A warp drains a window of pairs (at most
+// kRedWindowMax, fewer when the queue is short so every warp has one); each
+// lane carries kRedSlots pairs and takes the next pair of the window as soon
+// as one finishes, so a long walk holds up one slot, not the warp. Every
+// round issues one load or one atomicMin per live slot before any result is
+// used, so a lane's slots are in flight together.
+//
+// Root finding walks the larger of the two current nodes (labels decrease
+// towards a root, so the larger one cannot be an ancestor of the other):
+// meeting means one tree (Algorithm 1's label_1 == label_2, nothing to do);
+// reaching a root at the larger node means two trees, and that root is
+// linked by Algorithm 1's atomicMin loop under the other tree's root (link
+// mode 0) or under the other chain's current node (link mode 1).
 
 enum : int32_t { kTaskDone = 0, kTaskChase = 1, kTaskRoot = 2, kTaskMerge = 3 };
 
@@ -459,63 +484,92 @@ __device__ __forceinline__ int32_t red_load(const int32_t *p) { return __ldca(p)
 template <bool kBatched>
 __global__ void __launch_bounds__(256) k_reduce(Params P) {
     __shared__ long long s_pref[kMaxBands + 1];
-    if (threadIdx.x == 0) {
-        long long acc = 0;
-        for (int b = 0; b < P.n_bands; ++b) {
+    if (threadIdx.x < 32) {
+        // exclusive prefix of the band counts by warp 0: each lane sums a
+        // contiguous slice, then a warp scan of the slice totals
+        const int lane = threadIdx.x;
+        const int per = (P.n_bands + 31) / 32;
+        const int b0 = min(lane * per, P.n_bands), b1 = min(b0 + per, P.n_bands);
+        long long part = 0;
+        for (int b = b0; b < b1; ++b) part += (long long)P.band[b].cnt;
+        long long incl = part;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        long long acc = incl - part;
+        for (int b = b0; b < b1; ++b) {
             s_pref[b] = acc;
             acc += (long long)P.band[b].cnt;
         }
-        s_pref[P.n_bands] = acc;
+        if (lane == 31) s_pref[P.n_bands] = incl;
     }
     __syncthreads();
     const long long total = s_pref[P.n_bands];
-    const long long T = (long long)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    long long win = (total + nwarps - 1) / nwarps;
+    win = win < 64 ? 64 : (win > kRedWindowMax ? kRedWindowMax : win);
+    const long long nwin = (total + win - 1) / win;
 #ifdef CCL_DEVICE_STATS
     unsigned long long st_hops = 0, st_atom = 0, st_iter = 0;
 #endif
-    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    // a thread's kRedTasks pairs are consecutive queue entries (neighbouring
-    // sites, so their chains overlap in cache)
-    for (long long base = gtid * kRedTasks; base < total; base += (long long)kRedTasks * T) {
-        // task u: phase st, nodes a > b (chase: current nodes of the two
-        // chains; root: a = root of one tree, b walking to the other root;
-        // merge: Algorithm 1's label_1 = a, label_2 = b)
-        int32_t *L[kRedTasks];
-        int32_t cap[kRedTasks], a[kRedTasks], b[kRedTasks], it[kRedTasks], st[kRedTasks];
+    for (long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nwin; w += nwarps) {
+        const long long wbeg = w * win;
+        const long long wend = min(wbeg + win, total);
+        // band of the window's first pair (all lanes search; smem broadcast)
+        int band = 0;
+        {
+            int lo = 0, hi = P.n_bands - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_pref[mid] <= wbeg) lo = mid; else hi = mid - 1;
+            }
+            band = lo;
+        }
+        long long next = wbeg;
+        int32_t *L[kRedSlots];
+        int32_t cap[kRedSlots], a[kRedSlots], b[kRedSlots], it[kRedSlots], st[kRedSlots];
 #pragma unroll
-        for (int u = 0; u < kRedTasks; ++u) {
-            const long long p = base + u;
+        for (int u = 0; u < kRedSlots; ++u) {
             st[u] = kTaskDone;
             L[u] = P.one.labels;
             cap[u] = P.one.n;
-            a[u] = b[u] = 0;
-            it[u] = 0;
-            if (p < total) {
-                int lo = 0, hi = P.n_bands - 1;       // band of pair p
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (s_pref[mid] <= p) lo = mid; else hi = mid - 1;
-                }
-                const long long slot = P.band[lo].qbase + (p - s_pref[lo]);
-                const int2 pr = P.q[slot];
-                if (kBatched) {
-                    const int k = P.qk[slot];
-                    L[u] = P.insts[k].labels;
-                    cap[u] = P.insts[k].n;
-                }
-                a[u] = max(pr.x, pr.y);
-                b[u] = min(pr.x, pr.y);
-                st[u] = kTaskChase;
-            }
+            a[u] = b[u] = it[u] = 0;
         }
         for (;;) {
+            // refill empty slots with the window's next pairs, in order
+#pragma unroll
+            for (int u = 0; u < kRedSlots; ++u) {
+                const unsigned need = __ballot_sync(kFull, st[u] == kTaskDone);
+                const long long p = next + __popc(need & lt);
+                if (st[u] == kTaskDone && p < wend) {
+                    int bb = band;
+                    while (s_pref[bb + 1] <= p) ++bb;
+                    const long long slot = P.band[bb].qbase + (p - s_pref[bb]);
+                    const int2 pr = P.q[slot];
+                    if (kBatched) {
+                        const int k = P.qk[slot];
+                        L[u] = P.insts[k].labels;
+                        cap[u] = P.insts[k].n;
+                    }
+                    a[u] = max(pr.x, pr.y);
+                    b[u] = min(pr.x, pr.y);
+                    st[u] = kTaskChase;
+                    it[u] = 0;
+                }
+                next = min(next + (long long)__popc(need), wend);
+                while (band < P.n_bands - 1 && s_pref[band + 1] <= next) ++band;
+            }
 #ifdef CCL_DEVICE_STATS
             st_iter++;
 #endif
-            // issue: one load or one atomicMin per live task
-            int32_t v[kRedTasks];
+            // issue: one load or one atomicMin per live slot
+            int32_t v[kRedSlots];
 #pragma unroll
-            for (int u = 0; u < kRedTasks; ++u) {
+            for (int u = 0; u < kRedSlots; ++u) {
                 if (st[u] == kTaskChase) v[u] = red_load(L[u] + a[u]);
                 else if (st[u] == kTaskRoot) v[u] = red_load(L[u] + b[u]);
                 else if (st[u] == kTaskMerge) v[u] = atomicMin(L[u] + a[u], b[u]);
@@ -524,29 +578,15 @@ __global__ void __launch_bounds__(256) k_reduce(Params P) {
             // use
             bool any = false;
 #pragma unroll
-            for (int u = 0; u < kRedTasks; ++u) {
+            for (int u = 0; u < kRedSlots; ++u) {
                 if (st[u] == kTaskChase) {
-                    // Root finding of Algorithm 1 for both ends at once. Labels
-                    // decrease towards a root, so the larger current node a
-                    // cannot be an ancestor of b: it is the one advanced.
-                    // Meeting means one tree (label_1 == label_2, nothing to
-                    // do); a root at a means two trees.
 #ifdef CCL_DEVICE_STATS
                     st_hops++;
 #endif
                     const int32_t y = v[u];
-                    if (y == a[u]) {
-                        // a is a root: Algorithm 1 links it under b's root
-                        // (link mode 0); link mode 1 links it under b itself,
-                        // which skips the walk to b's root
-                        st[u] = P.link_mode ? kTaskMerge : kTaskRoot;
-                        it[u] = 0;
-                    } else if (y == b[u]) {
-                        st[u] = kTaskDone;
-                    } else {
-                        a[u] = max(y, b[u]);
-                        b[u] = min(y, b[u]);
-                    }
+                    if (y == a[u]) st[u] = P.link_mode ? kTaskMerge : kTaskRoot;
+                    else if (y == b[u]) st[u] = kTaskDone;
+                    else { a[u] = max(y, b[u]); b[u] = min(y, b[u]); }
                 } else if (st[u] == kTaskRoot) {
 #ifdef CCL_DEVICE_STATS
                     st_hops++;
@@ -557,7 +597,7 @@ __global__ void __launch_bounds__(256) k_reduce(Params P) {
 #ifdef CCL_DEVICE_STATS
                     st_atom++;
 #endif
-                    // Algorithm 1's atomicMin outcome on label_1 = a, label_2 = b
+                    // Algorithm 1's atomicMin outcome on label_1 = a > label_2 = b
                     const int32_t old = v[u];
                     if (old == b[u] || old == a[u]) st[u] = kTaskDone;
                     else if (old > b[u]) a[u] = old;
@@ -569,13 +609,13 @@ __global__ void __launch_bounds__(256) k_reduce(Params P) {
                 }
                 any |= st[u] != kTaskDone;
             }
-            if (!any) break;
+            if (!__any_sync(kFull, any) && next >= wend) break;
         }
     }
 #ifdef CCL_DEVICE_STATS
     if (st_hops) atomicAdd(P.counters + 1, st_hops);
     if (st_atom) atomicAdd(P.counters + 2, st_atom);
-    if (st_iter) atomicAdd(P.counters + 3, st_iter);
+    if (lane == 0 && st_iter) atomicAdd(P.counters + 3, st_iter);
 #endif
 }
 

@@ -24,10 +24,18 @@ constexpr int kBitBuf = kColCap / 32 + 12;
 constexpr int kRowRegs = 8;                // rows up to this degree are scanned in registers
 
 // steps (ii)/(iv): chunks a warp walks at once
-constexpr int kAnaChunks = 4;
+#ifndef CCL_ANA_CHUNKS
+#define CCL_ANA_CHUNKS 2
+#endif
+constexpr int kAnaChunks = CCL_ANA_CHUNKS;
 
-// step (iii): pairs a thread carries at once; most step-(i) CTAs (bands)
-constexpr int kRedTasks = 4;
+// step (iii): pairs a lane carries at once; pairs a warp drains per window;
+// most step-(i) CTAs (bands)
+#ifndef CCL_RED_SLOTS
+#define CCL_RED_SLOTS 4
+#endif
+constexpr int kRedSlots = CCL_RED_SLOTS;
+constexpr int kRedWindowMax = 2048;   // pairs per warp window (fewer for small queues)
 constexpr int kMaxBands = 1024;
 
 // latched device error bits
