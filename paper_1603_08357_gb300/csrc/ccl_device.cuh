@@ -248,26 +248,25 @@ __device__ __forceinline__ void init_consume_chunk(const Params &P, const Stage 
         a = __ldcs(I.row_ptr + min(i, slast));
         a_next = __ldcs(I.row_ptr + min(i + 1, slast));
     }
-    const bool ok = h.status == 0 && a >= h.e0 && a <= a_next && a_next <= h.e1;
-    const bool all_ok = __all_sync(kFull, ok);
-    if (lane == 0) {
-        if (s0 == 0 && a != 0) raise_err(P.err, kErrShape);
-        if (!all_ok) raise_err(P.err, kErrIndex);
+    // A row outside the tile's entry range, or running backwards, is read as
+    // empty and flagged; the rows of a valid input always pass.
+    if (!(a >= h.e0 && a <= a_next && a_next <= h.e1 && h.status == 0)) {
+        raise_err(P.err, kErrIndex);
+        a = a_next = h.e0 > 0 ? h.e0 : 0;
     }
-    if (lane == 31 && slast == n && a_next != I.nnz) raise_err(P.err, kErrShape);
-    if (!all_ok) a = a_next = 0;            // rows of a corrupt chunk are read as empty
     const int32_t beg = __shfl_sync(kFull, a, 0);
     const int32_t end = __shfl_sync(kFull, a_next, 31);
     const int32_t deg = a_next - a;
     const int32_t dmax = __reduce_max_sync(kFull, (uint32_t)deg);
-    const bool fast = dmax <= kRowRegs && beg >= h.ci_lo && end <= h.ci_hi && tc.rb0 + beg >= 0 &&
-                      tc.rb0 + end <= tc.nbits;
+    const bool fast = dmax <= kRowRegs && beg >= h.ci_lo && end <= h.ci_hi && a >= beg &&
+                      a_next <= end && tc.rb0 + beg >= 0 && tc.rb0 + end <= tc.nbits;
+    const bool all_fast = __all_sync(kFull, fast);
     int32_t m = INT32_MAX, cnt = 0;
     int32_t mk = -1;
     uint32_t resmask = 0;
     bool bad = false;
-    if (fast) {
-        const int32_t* col = S.ci + (a - h.ci_lo);
+    if (all_fast) {
+        const int32_t *col = S.ci + (a - h.ci_lo);
         uint32_t win = 0;
         if (deg > 0) {
             const int32_t rel = tc.rb0 + a;
@@ -295,7 +294,7 @@ __device__ __forceinline__ void init_consume_chunk(const Params &P, const Stage 
     if (bad) raise_err(P.err, kErrIndex);
     int32_t lab = cnt ? m : i;
     if (cnt) {
-        const int32_t mt = m / kTileSites;
+        const int32_t mt = (int32_t)((uint32_t)m / kTileSites);
         if (mt >= tc.vis_lo && mt <= tc.vis_hi) lab = __ldcg(I.labels + m);
     }
     if (i < n) I.labels[i] = lab;
@@ -311,8 +310,8 @@ __device__ __forceinline__ void init_consume_chunk(const Params &P, const Stage 
     if (r > 0) {
         int64_t slot = h.qband + (int64_t)base + (incl - r);
         if (slot + r > P.q_cap) { raise_err(P.err, kErrIndex); return; }   // corrupt rows only
-        if (fast) {
-            const int32_t* col = S.ci + (a - h.ci_lo);
+        if (all_fast) {
+            const int32_t *col = S.ci + (a - h.ci_lo);
             while (resmask) {
                 const int t = __ffs(resmask) - 1;
                 resmask &= resmask - 1;
@@ -370,6 +369,11 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
         }
         const Stage &S = st[s];
         const Inst I = inst_of<kBatched>(P, S.h.k);
+        if (lane == 0 && warp == 0) {
+            // row_ptr[0] == 0 and row_ptr[n] == nnz, once per instance
+            if (S.h.s0 == 0 && S.h.e0 != 0) raise_err(P.err, kErrShape);
+            if (S.h.s0 + S.h.ts == I.n && S.h.e1 != I.nnz) raise_err(P.err, kErrShape);
+        }
         TileCtx tc;
         tc.rb0 = (int32_t)(I.bit_off - (S.h.w_lo << 5));
         tc.nbits = (int32_t)(32 * (S.h.w_hi - S.h.w_lo));
