@@ -131,6 +131,20 @@ CCL_API ccl_status ccl_label_batched(ccl_context *ctx, int32_t n_inst, const int
                              void *stream);
 
 /*
+ * ccl_label_random -- ccl_label with the bonds drawn on the device instead of
+ * read from open_bits: the realisation of bond percolation (Section 4) with
+ * open probability p for seed `seed`. The bond {i, j} (i < j) is open iff
+ * (SplitMix64 output number i * 2^32 + j of the generator started from state
+ * `seed`) >> 11, times 2^-53, is below p (SplitMix64: Steele, Lea & Flood
+ * 2014; output number k is mix(seed + (k + 1) * 0x9E3779B97F4A7C15)). Only the
+ * CSR structure is read, so many realisations of one graph need only new
+ * seeds. 0 <= p <= 1. Asynchronous on `stream`; never replays a graph.
+ */
+CCL_API ccl_status ccl_label_random(ccl_context *ctx, int32_t n_sites, int64_t nnz, const int32_t *row_ptr,
+                                    const int32_t *col_idx, uint64_t seed, double p, int32_t *labels,
+                                    void *stream);
+
+/*
  * ccl_label_host -- ccl_label on HOST arrays: copies the inputs to context
  * buffers, labels, copies the labels back and waits. Synchronous. Pinned
  * (page-locked) host memory gives the full copy bandwidth.
@@ -185,6 +199,33 @@ CCL_API ccl_status ccl_sync(ccl_context *ctx, void *stream, int64_t timeout_ms);
  */
 CCL_API ccl_status ccl_validate(ccl_context *ctx, int32_t n_sites, int64_t nnz, const int32_t *row_ptr,
                         const int32_t *col_idx, const uint32_t *open_bits, void *stream);
+
+/*
+ * ccl_relabel -- sequential cluster numbers from canonical labels (the
+ * renumbering mentioned at the end of Section 3): seq[i] = number of clusters
+ * whose smallest site is below label[i], so clusters are numbered 0..C-1 in
+ * the order of their smallest sites.
+ *   labels      DEVICE int32[n], canonical labels (ccl_label output)
+ *   seq         DEVICE int32[n], output; must not alias labels
+ *   n_clusters  DEVICE int32, output: C
+ *   sizes       DEVICE int32[n] or NULL: sizes[c] = sites of cluster c (c < C)
+ * Asynchronous on `stream`; labels that are not canonical give undefined ids.
+ */
+CCL_API ccl_status ccl_relabel(ccl_context *ctx, int32_t n, const int32_t *labels, int32_t *seq,
+                               int32_t *n_clusters, int32_t *sizes, void *stream);
+
+/*
+ * ccl_spanning -- the spanning test of Section 4: *result = the smallest label
+ * carried both by a site of `top` and by a site of `bottom` (a cluster that
+ * connects the two sets), or -1 if there is none.
+ *   labels  DEVICE int32[n]; top DEVICE int32[n_top]; bottom DEVICE int32[n_bottom]
+ *   result  DEVICE int32
+ * Out-of-range site numbers are skipped and latched as
+ * CCL_ERR_INDEX_OUT_OF_RANGE (ccl_sync). Asynchronous on `stream`.
+ */
+CCL_API ccl_status ccl_spanning(ccl_context *ctx, int32_t n, const int32_t *labels, const int32_t *top,
+                                int32_t n_top, const int32_t *bottom, int32_t n_bottom, int32_t *result,
+                                void *stream);
 
 /* Counters of the last completed labelling call (synchronous read). */
 typedef struct {

@@ -58,6 +58,11 @@ def _load():
                 f.argtypes = sig
             lib.oracle_steps_label.restype = ctypes.c_int
             lib.oracle_steps_label.argtypes = sig + [P, P, P, P, P, P]
+            lib.oracle_splitmix64.restype = ctypes.c_uint64
+            lib.oracle_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+            lib.oracle_keyed_bits.restype = ctypes.c_int
+            lib.oracle_keyed_bits.argtypes = [ctypes.c_int32, ctypes.c_int64, P, P, ctypes.c_uint64,
+                                              ctypes.c_double, P]
             lib.oracle_uf_label_batched.restype = ctypes.c_int
             lib.oracle_uf_label_batched.argtypes = [ctypes.c_int32, ctypes.c_int32, P, P, P, P, P, P]
             _lib = lib
@@ -119,6 +124,20 @@ def steps_label(lat) -> dict:
     residual = [rj[rptr[i]:rptr[i + 1]].copy() for i in range(n)] if n <= 100_000 else None
     return dict(label=out, after_init=a0, after_ii=a1, after_iii=a2, residual=residual,
                 n_residual=int(nres.value))
+
+
+def splitmix64(seed: int, k: int) -> int:
+    return int(_load().oracle_splitmix64(seed & (2**64 - 1), k))
+
+
+def keyed_bits(lat, seed: int, p: float) -> np.ndarray:
+    """Open bits of the realisation (seed, p) whose bond {lo, hi} is drawn from
+    SplitMix64 output number lo * 2^32 + hi (the library's ccl_label_random)."""
+    rp, ci, _ = _args(lat)
+    bits = np.zeros(max(1, (lat.nnz + 31) // 32), np.uint32)
+    _check(_load().oracle_keyed_bits(lat.n, lat.nnz, _ptr(rp), _ptr(ci), seed & (2**64 - 1), float(p),
+                                     _ptr(bits)))
+    return bits
 
 
 def uf_label_batched(batch, k0: int = 0, k1: int | None = None) -> np.ndarray:

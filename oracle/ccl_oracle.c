@@ -206,6 +206,35 @@ int oracle_steps_label(int32_t n, int64_t nnz, const int32_t *row_ptr, const int
     return 0;
 }
 
+/* ---------------- bonds drawn from a counter-based generator ----------------- */
+
+/* SplitMix64 (Steele, Lea & Flood 2014; the reference implementation adds
+ * 0x9E3779B97F4A7C15 to the state and mixes): output number k (k >= 0) of the
+ * generator started from state `seed`. */
+uint64_t oracle_splitmix64(uint64_t seed, uint64_t k) {
+    uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* The realisation a graph gets when its bonds are drawn from (seed, p): the
+ * bond {lo, hi} is open iff (output number lo * 2^32 + hi) >> 11, scaled by
+ * 2^-53, is below p. Writes one bit per CSR entry (both copies of a bond get
+ * the same bit). bits must hold ceil(nnz / 32) zeroed words. */
+int oracle_keyed_bits(int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
+                      uint64_t seed, double p, uint32_t *bits) {
+    if (check_csr(n, nnz, row_ptr, col_idx)) return -1;
+    for (int32_t i = 0; i < n; ++i)
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const int32_t j = col_idx[e];
+            const uint64_t lo = (uint64_t)(j < i ? j : i), hi = (uint64_t)(j < i ? i : j);
+            const uint64_t out = oracle_splitmix64(seed, (lo << 32) | hi);
+            if ((double)(out >> 11) * 0x1.0p-53 < p) bits[e >> 5] |= 1u << (e & 31);
+        }
+    return 0;
+}
+
 /* ---------------- batched: K instances in concatenated form ------------------ */
 
 /* Instance k: sites [site_off[k], site_off[k+1]), local row pointers at

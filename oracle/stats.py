@@ -20,6 +20,19 @@ def cluster_sizes(labels: np.ndarray) -> np.ndarray:
     return np.bincount(labels, minlength=labels.size)
 
 
+def sequential(labels: np.ndarray):
+    """Clusters numbered 0..C-1 in the order of their smallest sites, and their
+    sizes: np.unique sorts the distinct canonical labels ascending."""
+    uniq, inverse, counts = np.unique(labels, return_inverse=True, return_counts=True)
+    return inverse.astype(np.int32), counts.astype(np.int32)
+
+
+def spanning_label(labels: np.ndarray, top: np.ndarray, bottom: np.ndarray) -> int:
+    """The smallest label present among both the top and the bottom sites, or -1."""
+    both = np.intersect1d(labels[top], labels[bottom])
+    return int(both.min()) if both.size else -1
+
+
 def spans(labels: np.ndarray, top: np.ndarray, bottom: np.ndarray) -> bool:
     """A cluster spans if it holds a site of the first row and one of the last
     row (open boundaries in the spanning direction, periodic across it)."""

@@ -89,8 +89,11 @@ def _load() -> ctypes.CDLL:
         "ccl_label": (C, [P, I32, I64, P, P, P, P, P]),
         "ccl_label_batched": (C, [P, I32, P, P, P, P, P, P, P]),
         "ccl_label_host": (C, [P, I32, I64, P, P, P, P, P]),
+        "ccl_label_random": (C, [P, I32, I64, P, P, ctypes.c_uint64, ctypes.c_double, P, P]),
         "ccl_label_noalloc": (C, [I32, I64, P, P, P, P, P]),
         "ccl_reserve": (C, [P, I64, I64, I64]),
+        "ccl_relabel": (C, [P, I32, P, P, P, P, P]),
+        "ccl_spanning": (C, [P, I32, P, P, I32, P, I32, P, P]),
         "ccl_sync": (C, [P, P, I64]),
         "ccl_validate": (C, [P, I32, I64, P, P, P, P]),
         "ccl_get_stats": (C, [P, ctypes.POINTER(ccl_run_stats)]),
@@ -266,6 +269,13 @@ def ccl_label_batched(ctx, n_inst: int, site_off, ent_off, row_ptr, col_idx, ope
                                   _dev_ptr(labels, "labels", _i32()), _stream(stream))
 
 
+def ccl_label_random(ctx, n_sites: int, nnz: int, row_ptr, col_idx, seed: int, p: float, labels,
+                     stream=None) -> int:
+    return _lib.ccl_label_random(ctx, int(n_sites), int(nnz), _dev_ptr(row_ptr, "row_ptr", _i32()),
+                                 _dev_ptr(col_idx, "col_idx", _i32()), ctypes.c_uint64(seed & (2**64 - 1)),
+                                 float(p), _dev_ptr(labels, "labels", _i32()), _stream(stream))
+
+
 def ccl_label_host(ctx, n_sites: int, nnz: int, row_ptr, col_idx, open_bits, labels,
                    stream=None) -> int:
     return _lib.ccl_label_host(ctx, int(n_sites), int(nnz), _host_ptr(row_ptr, "row_ptr", np.int32),
@@ -284,6 +294,18 @@ def ccl_label_noalloc(n_sites: int, nnz: int, row_ptr, col_idx, open_bits, label
 
 def ccl_reserve(ctx, n_sites: int, nnz: int, n_chunks: int = 0) -> int:
     return _lib.ccl_reserve(ctx, int(n_sites), int(nnz), int(n_chunks))
+
+
+def ccl_relabel(ctx, n: int, labels, seq, n_clusters, sizes=None, stream=None) -> int:
+    return _lib.ccl_relabel(ctx, int(n), _dev_ptr(labels, "labels", _i32()), _dev_ptr(seq, "seq", _i32()),
+                            _dev_ptr(n_clusters, "n_clusters", _i32()), _dev_ptr(sizes, "sizes", _i32()),
+                            _stream(stream))
+
+
+def ccl_spanning(ctx, n: int, labels, top, n_top: int, bottom, n_bottom: int, result, stream=None) -> int:
+    return _lib.ccl_spanning(ctx, int(n), _dev_ptr(labels, "labels", _i32()), _dev_ptr(top, "top", _i32()),
+                             int(n_top), _dev_ptr(bottom, "bottom", _i32()), int(n_bottom),
+                             _dev_ptr(result, "result", _i32()), _stream(stream))
 
 
 def ccl_sync(ctx, stream=None, timeout_ms: int = -1) -> int:

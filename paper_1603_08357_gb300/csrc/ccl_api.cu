@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <array>
 #include <chrono>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -16,6 +17,7 @@
 #include <vector>
 
 #include "ccl_device.cuh"
+#include "ccl_stats.cuh"
 
 using namespace ccl;
 
@@ -66,6 +68,9 @@ struct ccl_context {
     // host-buffer path
     void *d_host_in = nullptr;
     int64_t host_in_cap = 0;
+    // relabel / spanning scratch
+    void *d_aux = nullptr;
+    int64_t aux_cap = 0;
     // options
     TuneChoice opt;
     int use_graphs = 1;
@@ -90,6 +95,7 @@ struct ccl_context {
 namespace {
 
 constexpr size_t kMaxGraphs = 16;
+constexpr uint64_t kNoGen = ~0ull;     // Params::gen_thr of calls that read open_bits
 constexpr int64_t kProfRing = 4096;
 
 ccl_status cuda_status(cudaError_t e) {
@@ -132,6 +138,7 @@ int blocks_per_sm(ccl_context *ctx, int kernel_id, int threads) {
         case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_analysis<true>, threads, 0); break;
         case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_reduce<false>, threads, 0); break;
         case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_reduce<true>, threads, 0); break;
+        case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init<false, true>, kInitThreads, kInitSmem); break;
         default: break;
     }
     if (e != cudaSuccess || nb < 1) { (void)cudaGetLastError(); nb = 1; }
@@ -217,6 +224,8 @@ ccl_status enqueue_steps(ccl_context *ctx, const Params &P0, bool batched, const
     if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[0], s));
     if (batched) {
         k_init<true><<<(unsigned)g_init, kInitThreads, kInitSmem, s>>>(P);
+    } else if (P.gen_thr != kNoGen) {
+        k_init<false, true><<<(unsigned)g_init, kInitThreads, kInitSmem, s>>>(P);
     } else {
         k_init<false><<<(unsigned)g_init, kInitThreads, kInitSmem, s>>>(P);
     }
@@ -296,8 +305,8 @@ bool stream_capturing(cudaStream_t s) {
 ccl_status run(ccl_context *ctx, Params P, bool batched, const TuneChoice &tc, cudaStream_t s,
                const std::vector<Inst> *table, uint64_t shape_hash, bool allow_graph = true,
                const std::vector<int64_t> *offsets = nullptr) {
-    for (int kid = 0; kid < 6; ++kid)
-        (void)blocks_per_sm(ctx, kid, kid < 2 ? kInitThreads : (kid >= 4 ? 256 : tc.threads));
+    for (int kid = 0; kid < 7; ++kid)
+        (void)blocks_per_sm(ctx, kid, (kid < 2 || kid == 6) ? kInitThreads : (kid >= 4 ? 256 : tc.threads));
     ctx->last.used_graph = 0;
     const bool capturing = stream_capturing(s);
     if (ctx->profile || !ctx->use_graphs || capturing || !allow_graph) {
@@ -392,6 +401,7 @@ Params base_params(ccl_context *ctx, const TuneChoice &tc) {
     P.q = ctx->d_q;
     P.qk = ctx->d_qk;
     P.q_cap = ctx->q_cap;
+    P.gen_thr = kNoGen;
     P.err = ctx->d_err;
     P.counters = ctx->d_counters;
     return P;
@@ -409,7 +419,8 @@ ccl_status check_single_args(ccl_context *ctx, int32_t n, int64_t nnz, const int
 
 ccl_status label_single(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
                         const int32_t *col_idx, const uint32_t *bits, int32_t *labels,
-                        cudaStream_t s, const TuneChoice &tc) {
+                        cudaStream_t s, const TuneChoice &tc, uint64_t gen_seed = 0,
+                        uint64_t gen_thr = kNoGen) {
     const int64_t chunks = ((int64_t)n + kChunk - 1) / kChunk;
     ccl_status st = ensure_workspace(ctx, nnz, false);
     if (st != CCL_OK) return st;
@@ -431,6 +442,12 @@ ccl_status label_single(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t 
     ctx->last.n_sites = n;
     ctx->last.nnz = nnz;
     ctx->last.n_inst = 1;
+    if (gen_thr != kNoGen) {
+        // bonds drawn on the device: a new seed every call, so no graph reuse
+        P.gen_seed = gen_seed;
+        P.gen_thr = gen_thr;
+        return run(ctx, P, false, tc, s, nullptr, 0, false);
+    }
     // the graph key covers every field of the instance (sizes included)
     return run(ctx, P, false, tc, s, nullptr, fnv1a(&P.one, sizeof(Inst)));
 }
@@ -515,6 +532,9 @@ ccl_status ccl_context_create(ccl_context **out, int device) {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_init<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kInitSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_init<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kInitSmem);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         ccl_context_destroy(ctx);
@@ -551,6 +571,7 @@ void ccl_context_destroy(ccl_context *ctx) {
     if (ctx->d_insts) cudaFree(ctx->d_insts);
     if (ctx->h_insts) cudaFreeHost(ctx->h_insts);
     if (ctx->d_host_in) cudaFree(ctx->d_host_in);
+    if (ctx->d_aux) cudaFree(ctx->d_aux);
     if (ctx->staging_free) cudaEventDestroy(ctx->staging_free);
     for (auto &set : ctx->prof)
         for (auto &e : set) if (e) cudaEventDestroy(e);
@@ -677,6 +698,78 @@ ccl_status ccl_label_batched(ccl_context *ctx, int32_t K, const int64_t *site_of
     return run(ctx, P, true, tc, (cudaStream_t)stream, &table, h, true, &offs);
 }
 
+ccl_status ccl_label_random(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
+                            const int32_t *col_idx, uint64_t seed, double p, int32_t *labels,
+                            void *stream) {
+    ccl_status st = check_single_args(ctx, n, nnz, row_ptr, col_idx, (const uint32_t *)1, labels);
+    if (st != CCL_OK || n == 0) return st;
+    if (!(p >= 0.0 && p <= 1.0)) return CCL_ERR_INVALID_ARGUMENT;
+    // open iff (output >> 11) * 2^-53 < p  <=>  (output >> 11) < ceil(p * 2^53)
+    const double scaled = std::ceil(p * 9007199254740992.0);
+    const uint64_t thr = (uint64_t)scaled;
+    DeviceGuard guard(ctx->device);
+    const TuneChoice tc = choice_for(ctx, n, nnz);
+    return label_single(ctx, n, nnz, row_ptr, col_idx, nullptr, labels, (cudaStream_t)stream, tc, seed, thr);
+}
+
+namespace {
+ccl_status ensure_aux(ccl_context *ctx, int64_t bytes) {
+    if (bytes <= ctx->aux_cap) return CCL_OK;
+    if (ctx->d_aux) cudaFree(ctx->d_aux);
+    ctx->d_aux = nullptr;
+    ctx->aux_cap = 0;
+    CCL_CUDA(cudaMalloc(&ctx->d_aux, (size_t)bytes));
+    ctx->aux_cap = bytes;
+    return CCL_OK;
+}
+}  // namespace
+
+ccl_status ccl_relabel(ccl_context *ctx, int32_t n, const int32_t *labels, int32_t *seq,
+                       int32_t *n_clusters, int32_t *sizes, void *stream) {
+    if (!ctx || n < 0 || !n_clusters) return CCL_ERR_INVALID_ARGUMENT;
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) {
+        CCL_CUDA(cudaMemsetAsync(n_clusters, 0, sizeof(int32_t), s));
+        return CCL_OK;
+    }
+    if (!labels || !seq || labels == seq) return CCL_ERR_INVALID_ARGUMENT;
+    const int64_t nb = ((int64_t)n + kRelBlock - 1) / kRelBlock;
+    ccl_status st = ensure_aux(ctx, nb * (int64_t)sizeof(int32_t));
+    if (st != CCL_OK) return st;
+    int32_t *cnt = (int32_t *)ctx->d_aux;
+    k_root_counts<<<(unsigned)nb, kRelThreads, 0, s>>>(n, labels, cnt);
+    k_scan_counts<<<1, 1024, 0, s>>>((int32_t)nb, cnt, n_clusters);
+    k_root_ids<<<(unsigned)nb, kRelThreads, 0, s>>>(n, labels, cnt, seq, sizes);
+    const int64_t g = std::min<int64_t>((int64_t)ctx->num_sms * 8, ((int64_t)n + 255) / 256);
+    k_site_ids<<<(unsigned)g, 256, 0, s>>>(n, labels, seq);
+    if (sizes) k_sizes<<<(unsigned)g, 256, 0, s>>>(n, seq, sizes);
+    CCL_CUDA(cudaGetLastError());
+    return CCL_OK;
+}
+
+ccl_status ccl_spanning(ccl_context *ctx, int32_t n, const int32_t *labels, const int32_t *top,
+                        int32_t n_top, const int32_t *bottom, int32_t n_bottom, int32_t *result,
+                        void *stream) {
+    if (!ctx || n < 0 || n_top < 0 || n_bottom < 0 || !result) return CCL_ERR_INVALID_ARGUMENT;
+    if (n > 0 && !labels) return CCL_ERR_INVALID_ARGUMENT;
+    if ((n_top > 0 && !top) || (n_bottom > 0 && !bottom)) return CCL_ERR_INVALID_ARGUMENT;
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t words = ((int64_t)n + 31) / 32;
+    ccl_status st = ensure_aux(ctx, std::max<int64_t>(words, 1) * (int64_t)sizeof(uint32_t));
+    if (st != CCL_OK) return st;
+    uint32_t *flags = (uint32_t *)ctx->d_aux;
+    if (words) CCL_CUDA(cudaMemsetAsync(flags, 0, (size_t)words * sizeof(uint32_t), s));
+    const int64_t gt = std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms * 4, ((int64_t)n_top + 255) / 256));
+    const int64_t gb = std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms * 4, ((int64_t)n_bottom + 255) / 256));
+    k_span_mark<<<(unsigned)gt, 256, 0, s>>>(n, labels, top, n_top, flags, result, ctx->d_err);
+    k_span_check<<<(unsigned)gb, 256, 0, s>>>(n, labels, bottom, n_bottom, flags, result, ctx->d_err);
+    k_span_finish<<<1, 1, 0, s>>>(result);
+    CCL_CUDA(cudaGetLastError());
+    return CCL_OK;
+}
+
 ccl_status ccl_sync(ccl_context *ctx, void *stream, int64_t timeout_ms) {
     if (!ctx) return CCL_ERR_INVALID_ARGUMENT;
     DeviceGuard guard(ctx->device);
@@ -719,6 +812,7 @@ ccl_status ccl_label_host(ccl_context *ctx, int32_t n, int64_t nnz, const int32_
     if ((int64_t)need > ctx->host_in_cap) {
         CCL_CUDA(cudaStreamSynchronize(s));
         if (ctx->d_host_in) cudaFree(ctx->d_host_in);
+    if (ctx->d_aux) cudaFree(ctx->d_aux);
         ctx->d_host_in = nullptr;
         ctx->host_in_cap = 0;
         drop_graphs(ctx);    // graphs may hold pointers into the old buffer

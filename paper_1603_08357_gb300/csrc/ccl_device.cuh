@@ -38,6 +38,20 @@ __device__ __forceinline__ void raise_err(unsigned *err, unsigned bit) {
     if ((*(volatile unsigned *)err & bit) == 0) atomicOr(err, bit);
 }
 
+// Bond state drawn on the device. SplitMix64 (Steele, Lea & Flood 2014) in
+// counter form: output number `key` of the generator started from state `seed`
+// is mix(seed + (key + 1) * 0x9E3779B97F4A7C15); the bond {lo, hi} (lo < hi)
+// has key lo * 2^32 + hi and is open iff (output >> 11) < thr, i.e. iff
+// (output >> 11) * 2^-53 < p for thr = ceil(p * 2^53).
+__device__ __forceinline__ bool gen_bond_open(uint64_t seed, uint64_t thr, uint32_t lo, uint32_t hi) {
+    const uint64_t key = ((uint64_t)lo << 32) | hi;
+    uint64_t z = seed + (key + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (z >> 11) < thr;
+}
+
 // largest k with insts[k].chunk_begin <= c (instances ordered)
 __device__ __forceinline__ int find_inst(const Params &P, int64_t c) {
     int lo = 0, hi = P.K - 1;
@@ -142,7 +156,7 @@ __device__ __forceinline__ void cta_band(int64_t n_tiles, int64_t &band_lo, int6
     band_hi = min(band_lo + per, n_tiles);
 }
 
-template <bool kBatched>
+template <bool kBatched, bool kGen = false>
 __device__ __forceinline__ void init_produce(const Params &P, Stage *st, uint64_t *full,
                                              uint64_t *empty) {
     int64_t band_lo, band_hi;
@@ -179,7 +193,7 @@ __device__ __forceinline__ void init_produce(const Params &P, Stage *st, uint64_
             h.ci_lo = (int32_t)lo;
             h.ci_hi = (int32_t)hi;
             const int64_t w0 = (I.bit_off + h.e0) >> 5;
-            const int64_t w1 = h.e1 > h.e0 ? ((I.bit_off + h.e1 - 1) >> 5) + 1 : w0;
+            const int64_t w1 = (h.e1 > h.e0 && !kGen) ? ((I.bit_off + h.e1 - 1) >> 5) + 1 : w0;
             copy_window(I.bits, w0, w1, I.bits_lo, I.bits_hi, kBitBuf, h.w_lo, h.w_hi);
         } else {
             h.ci_lo = h.ci_hi = 0;
@@ -198,17 +212,27 @@ __device__ __forceinline__ void init_produce(const Params &P, Stage *st, uint64_
 
 // General scan of one lane's row (rows longer than kRowRegs, or parts of the
 // input outside the shared-memory copy): per-entry bounds-checked reads.
-__device__ __forceinline__ void scan_row_general(const Stage &S, const Inst &I, int32_t a, int32_t a_next,
-                                                 int32_t i, int32_t &m, int32_t &mk, int32_t &cnt,
-                                                 bool &bad) {
+// the open bit of local entry e of instance I (row i, column j < i)
+template <bool kGen>
+__device__ __forceinline__ bool entry_open(const Params &P, const Stage &S, const Inst &I, int32_t e,
+                                           int32_t i, int32_t j) {
+    if (kGen) return gen_bond_open(P.gen_seed, P.gen_thr, (uint32_t)j, (uint32_t)i);
+    const StageHdr &h = S.h;
+    const int64_t ge = I.bit_off + e;
+    const int64_t we = ge >> 5;
+    const uint32_t w = (we >= h.w_lo && we < h.w_hi) ? S.bw[we - h.w_lo] : __ldg(I.bits + we);
+    return (w >> (ge & 31)) & 1u;
+}
+
+template <bool kGen>
+__device__ __forceinline__ void scan_row_general(const Params &P, const Stage &S, const Inst &I, int32_t a,
+                                                 int32_t a_next, int32_t i, int32_t &m, int32_t &mk,
+                                                 int32_t &cnt, bool &bad) {
     const StageHdr &h = S.h;
     for (int32_t e = a; e < a_next; ++e) {
-        const int64_t ge = I.bit_off + e;
         const int32_t j = (e >= h.ci_lo && e < h.ci_hi) ? S.ci[e - h.ci_lo] : __ldg(I.col_idx + e);
-        const int64_t we = ge >> 5;
-        const uint32_t w = (we >= h.w_lo && we < h.w_hi) ? S.bw[we - h.w_lo] : __ldg(I.bits + we);
         bad |= (uint32_t)j >= (uint32_t)I.n;
-        if (((w >> (ge & 31)) & 1u) && (uint32_t)j < (uint32_t)i) {
+        if ((uint32_t)j < (uint32_t)i && entry_open<kGen>(P, S, I, e, i, j)) {
             ++cnt;
             if (j < m) { m = j; mk = e; }
         }
@@ -230,7 +254,7 @@ struct TileCtx {
 // stage barriers): a site whose smallest open lower neighbour m lies in such
 // a tile takes label[m] (the root of m's tree after steps (i)/(ii)) instead of
 // m, which shortcuts the chain step (ii) would walk.
-template <bool kBatched>
+template <bool kBatched, bool kGen = false>
 __device__ __forceinline__ void init_consume_chunk(const Params &P, const Stage &S, const Inst &I,
                                                    int cc, int lane, const TileCtx &tc,
                                                    unsigned long long *band_cnt,
@@ -259,7 +283,7 @@ __device__ __forceinline__ void init_consume_chunk(const Params &P, const Stage 
     const int32_t deg = a_next - a;
     const int32_t dmax = __reduce_max_sync(kFull, (uint32_t)deg);
     const bool fast = dmax <= kRowRegs && beg >= h.ci_lo && end <= h.ci_hi && a >= beg &&
-                      a_next <= end && tc.rb0 + beg >= 0 && tc.rb0 + end <= tc.nbits;
+                      a_next <= end && (kGen || (tc.rb0 + beg >= 0 && tc.rb0 + end <= tc.nbits));
     const bool all_fast = __all_sync(kFull, fast);
     int32_t m = INT32_MAX, cnt = 0;
     int32_t mk = -1;
@@ -268,7 +292,7 @@ __device__ __forceinline__ void init_consume_chunk(const Params &P, const Stage 
     if (all_fast) {
         const int32_t *col = S.ci + (a - h.ci_lo);
         uint32_t win = 0;
-        if (deg > 0) {
+        if (!kGen && deg > 0) {
             const int32_t rel = tc.rb0 + a;
             win = __funnelshift_r(S.bw[rel >> 5], S.bw[(rel + deg - 1) >> 5], (uint32_t)rel & 31u);
         }
@@ -279,7 +303,10 @@ __device__ __forceinline__ void init_consume_chunk(const Params &P, const Stage 
             if (t < deg) {
                 const int32_t j = col[t];
                 jmax = max(jmax, (uint32_t)j);
-                if (((win >> t) & 1u) && (uint32_t)j < (uint32_t)i) {
+                const bool open = kGen ? ((uint32_t)j < (uint32_t)i &&
+                                          gen_bond_open(P.gen_seed, P.gen_thr, (uint32_t)j, (uint32_t)i))
+                                       : ((win >> t) & 1u) != 0;
+                if (open && (uint32_t)j < (uint32_t)i) {
                     lowmask |= 1u << t;
                     if (j < m) { m = j; mk = t; }
                 }
@@ -289,7 +316,7 @@ __device__ __forceinline__ void init_consume_chunk(const Params &P, const Stage 
         cnt = __popc(lowmask);
         resmask = cnt ? (lowmask & ~(1u << mk)) : 0u;
     } else {
-        scan_row_general(S, I, a, a_next, i, m, mk, cnt, bad);
+        scan_row_general<kGen>(P, S, I, a, a_next, i, m, mk, cnt, bad);
     }
     if (bad) raise_err(P.err, kErrIndex);
     int32_t lab = cnt ? m : i;
@@ -321,11 +348,8 @@ __device__ __forceinline__ void init_consume_chunk(const Params &P, const Stage 
             }
         } else {
             for (int32_t e = a; e < a_next; ++e) {
-                const int64_t ge = I.bit_off + e;
                 const int32_t j = (e >= h.ci_lo && e < h.ci_hi) ? S.ci[e - h.ci_lo] : __ldg(I.col_idx + e);
-                const int64_t we = ge >> 5;
-                const uint32_t w = (we >= h.w_lo && we < h.w_hi) ? S.bw[we - h.w_lo] : __ldg(I.bits + we);
-                if (((w >> (ge & 31)) & 1u) && (uint32_t)j < (uint32_t)i && e != mk) {
+                if ((uint32_t)j < (uint32_t)i && e != mk && entry_open<kGen>(P, S, I, e, i, j)) {
                     P.q[slot] = make_int2(i, j);
                     if (kBatched) P.qk[slot] = h.k;
                     ++slot;
@@ -335,7 +359,7 @@ __device__ __forceinline__ void init_consume_chunk(const Params &P, const Stage 
     }
 }
 
-template <bool kBatched>
+template <bool kBatched, bool kGen = false>
 __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
@@ -354,7 +378,7 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
     if (threadIdx.x == 0) band_cnt = 0;
     __syncthreads();
     if (warp == kInitConsumers) {               // producer warp
-        if (lane == 0) init_produce<kBatched>(P, st, full, empty);
+        if (lane == 0) init_produce<kBatched, kGen>(P, st, full, empty);
         return;
     }
     unsigned long long my_pairs = 0;
@@ -387,7 +411,7 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
         for (int q = 0; q < kChunksPerConsumer; ++q) {
             const int cc = warp * kChunksPerConsumer + q;
             if (cc * kChunk >= S.h.ts) break;
-            init_consume_chunk<kBatched>(P, S, I, cc, lane, tc, &band_cnt, my_pairs);
+            init_consume_chunk<kBatched, kGen>(P, S, I, cc, lane, tc, &band_cnt, my_pairs);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);

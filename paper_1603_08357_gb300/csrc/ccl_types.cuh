@@ -81,6 +81,8 @@ struct Params {
     int2 *q;                   // residual pairs (i, j); slots indexed by global CSR entry
     int32_t *qk;               // instance of each pair (K > 1 only)
     int64_t q_cap;             // slots of q (and qk)
+    uint64_t gen_seed;         // bonds drawn on the device: SplitMix64 state ...
+    uint64_t gen_thr;          // ... and threshold (bond open iff output >> 11 < gen_thr)
     unsigned *err;
     unsigned long long *counters;   // [0] residual pairs
 };

@@ -1,0 +1,91 @@
+"""GPU parity of the steps around the labelling: bonds drawn on the device
+(ccl_label_random), sequential relabelling with cluster sizes (ccl_relabel)
+and the spanning test of Section 4 (ccl_spanning), each against the oracle."""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+import lattices as L
+import oracle
+from oracle import stats
+import paper_1603_08357_gb300 as ccl
+from ccl_testutil import DEV, gpu_label, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _random_labels(ctx, lat, seed, p):
+    rp, ci, _ = to_dev(lat)
+    out = torch.full((max(lat.n, 1),), -3, dtype=torch.int32, device=DEV)
+    st = ccl.ccl_label_random(ctx, lat.n, lat.nnz, rp, ci if lat.nnz else None, seed, p, out)
+    assert st == ccl.CCL_OK, ccl.ccl_status_string(st)
+    assert ccl.ccl_sync(ctx) == ccl.CCL_OK
+    return out[:lat.n].cpu().numpy()
+
+
+@pytest.mark.parametrize("kind,kw", [("triangle", dict(L=300)), ("honeycomb", dict(L=211)),
+                                     ("cayley", dict(z=3, shells=14, perm_seed=4)),
+                                     ("triangle", dict(L=257, periodic_y=False))])
+@pytest.mark.parametrize("p", [0.0, 0.35, 0.5, 0.65, 1.0])
+def test_label_random_matches_oracle(ctx, kind, kw, p):
+    lat = L.make_instance(dict(kind=kind, p=0.5, seed=1, **kw))
+    for seed in (7, 2**63 + 11):
+        want = oracle.uf_label(dataclasses.replace(lat, open_bits=oracle.keyed_bits(lat, seed, p)))
+        assert np.array_equal(_random_labels(ctx, lat, seed, p), want)
+
+
+def test_label_random_multigraph(ctx):
+    lat = L.random_graph(5000, 9000, 3, asymmetric=0.0)
+    for seed in range(5):
+        want = oracle.uf_label(dataclasses.replace(lat, open_bits=oracle.keyed_bits(lat, seed, 0.55)))
+        assert np.array_equal(_random_labels(ctx, lat, seed, 0.55), want)
+    rp, ci, _ = to_dev(lat)
+    out = torch.empty(lat.n, dtype=torch.int32, device=DEV)
+    assert ccl.ccl_label_random(ctx, lat.n, lat.nnz, rp, ci, 1, 1.5, out) == ccl.CCL_ERR_INVALID_ARGUMENT
+
+
+@pytest.mark.parametrize("kind,kw,p", [("triangle", dict(L=513), L.PC_TRIANGLE),
+                                       ("honeycomb", dict(L=300), 0.8),
+                                       ("cayley", dict(z=4, shells=9, perm_seed=2), 1 / 3),
+                                       ("triangle", dict(L=40), 0.0), ("triangle", dict(L=40), 1.0)])
+def test_relabel_and_sizes(ctx, kind, kw, p):
+    lat = L.make_instance(dict(kind=kind, p=p, seed=5, **kw))
+    lab = gpu_label(ctx, lat)
+    d_lab = torch.from_numpy(lab).to(DEV)
+    seq = torch.full((lat.n,), -1, dtype=torch.int32, device=DEV)
+    sizes = torch.full((lat.n,), -1, dtype=torch.int32, device=DEV)
+    nc = torch.zeros(1, dtype=torch.int32, device=DEV)
+    assert ccl.ccl_relabel(ctx, lat.n, d_lab, seq, nc, sizes) == ccl.CCL_OK
+    assert ccl.ccl_sync(ctx) == ccl.CCL_OK
+    want_seq, want_sizes = stats.sequential(lab)
+    C = int(nc.item())
+    assert C == want_sizes.size == stats.n_clusters(lab)
+    assert np.array_equal(seq.cpu().numpy(), want_seq)
+    assert np.array_equal(sizes[:C].cpu().numpy(), want_sizes)
+    assert ccl.ccl_relabel(ctx, lat.n, d_lab, d_lab, nc) == ccl.CCL_ERR_INVALID_ARGUMENT
+
+
+@pytest.mark.parametrize("kind", ["triangle", "honeycomb"])
+def test_spanning(ctx, kind):
+    pc = L.PC_TRIANGLE if kind == "triangle" else L.PC_HONEYCOMB
+    for Ls, seed in ((64, 1), (200, 2), (513, 3)):
+        for p in (pc - 0.05, pc, pc + 0.05):
+            lat = L.make_instance(dict(kind=kind, L=Ls, p=p, seed=seed, periodic_y=False))
+            lab = gpu_label(ctx, lat)
+            top, bot = L.row_sites(lat, 0), L.row_sites(lat, Ls - 1)
+            res = torch.zeros(1, dtype=torch.int32, device=DEV)
+            d_lab = torch.from_numpy(lab).to(DEV)
+            d_top = torch.from_numpy(top.astype(np.int32)).to(DEV)
+            d_bot = torch.from_numpy(bot.astype(np.int32)).to(DEV)
+            assert ccl.ccl_spanning(ctx, lat.n, d_lab, d_top, top.size, d_bot, bot.size, res) == ccl.CCL_OK
+            assert ccl.ccl_sync(ctx) == ccl.CCL_OK
+            assert int(res.item()) == stats.spanning_label(oracle.uf_label(lat), top, bot)
+
+
+def test_random_full_size_triangle(ctx):
+    """tri4096 at p_c with device-drawn bonds, compared site by site."""
+    lat = L.triangle(4096, 0.5, 2)
+    want = oracle.uf_label(dataclasses.replace(lat, open_bits=oracle.keyed_bits(lat, 99, 0.3473)))
+    assert np.array_equal(_random_labels(ctx, lat, 99, 0.3473), want)

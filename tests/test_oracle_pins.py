@@ -231,3 +231,37 @@ def test_batched_oracle_matches_single():
     for k in range(b.k):
         s0, s1 = b.site_off[k], b.site_off[k + 1]
         assert np.array_equal(lab[s0:s1], oracle.bfs_label(b.instance(k)))
+
+
+def test_oracle_splitmix64_published_vectors():
+    # first outputs of SplitMix64 from state 0, as printed by the reference implementation
+    assert oracle.splitmix64(0, 0) == 0xE220A8397B1DCDAF
+    assert oracle.splitmix64(0, 1) == 0x6E789E6AA1B965F4
+    assert oracle.splitmix64(0, 2) == 0x06C45D188009454F
+
+
+def test_keyed_bits_symmetric_and_rate():
+    import dataclasses
+    tri = L.triangle(128, 0.5, 1)
+    for p in (0.0, 0.3, 0.65, 1.0):
+        bits = oracle.keyed_bits(tri, 12345, p)
+        lat = dataclasses.replace(tri, open_bits=bits)
+        b = L.unpack_bits(bits, lat.nnz)
+        rows = np.repeat(np.arange(lat.n), np.diff(lat.row_ptr))
+        state = {}
+        for r, c, v in zip(rows.tolist(), lat.col_idx.tolist(), b.tolist()):
+            key = (min(r, c), max(r, c))
+            assert state.setdefault(key, v) == v          # both copies agree
+        frac = np.mean(list(state.values()))
+        assert abs(frac - p) <= 4 * np.sqrt(max(p * (1 - p), 1e-9) / len(state)) + 1e-12
+
+
+def test_sequential_and_spanning_by_hand():
+    g = load_golden("worked_example.txt")
+    seq, sizes = stats.sequential(np.array(g["label"], np.int32))
+    assert seq.tolist() == [0, 0, 1, 1, 0, 0, 1, 1, 0, 1]          # worked by hand
+    assert sizes.tolist() == [5, 5]
+    lab = np.array([0, 0, 2, 2, 4, 0], np.int32)                    # clusters {0,1,5}, {2,3}, {4}
+    assert stats.spanning_label(lab, np.array([1, 2]), np.array([5, 4])) == 0
+    assert stats.spanning_label(lab, np.array([2]), np.array([3, 4])) == 2
+    assert stats.spanning_label(lab, np.array([4]), np.array([0, 2])) == -1
