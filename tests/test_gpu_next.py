@@ -89,3 +89,40 @@ def test_random_full_size_triangle(ctx):
     lat = L.triangle(4096, 0.5, 2)
     want = oracle.uf_label(dataclasses.replace(lat, open_bits=oracle.keyed_bits(lat, 99, 0.3473)))
     assert np.array_equal(_random_labels(ctx, lat, 99, 0.3473), want)
+
+
+def test_spanning_curve_matches_oracle(ctx):
+    """R_span(p) from the device sampler equals, realisation by realisation,
+    the oracle's labels of the same keyed bonds."""
+    from paper_1603_08357_gb300 import percolation as P
+    for kind, Ls in (("triangle", 24), ("honeycomb", 17)):
+        lat = L.make_instance(dict(kind=kind, L=Ls, p=0.0, seed=0, periodic_y=False))
+        top, bot = P.boundary_rows(kind, Ls)
+        assert np.array_equal(np.sort(top), np.sort(L.row_sites(lat, 0)))
+        assert np.array_equal(np.sort(bot), np.sort(L.row_sites(lat, Ls - 1)))
+        ps = [P.PC_EXACT[kind] - 0.1, P.PC_EXACT[kind], P.PC_EXACT[kind] + 0.1]
+        R = P.Sampler(ctx, lat, top, bot).spanning_curve(ps, 120, seed0=500)
+        want = []
+        for p in ps:
+            hits = 0
+            for r in range(120):
+                lab = oracle.uf_label(dataclasses.replace(lat, open_bits=oracle.keyed_bits(lat, 500 + r, p)))
+                hits += stats.spanning_label(lab, top, bot) >= 0
+            want.append(hits / 120)
+        assert np.allclose(R, want, rtol=0, atol=1e-12), (kind, R, want)
+
+
+def test_spanning_crossing_near_exact_threshold(ctx):
+    """Curves of two sizes cross near 2 sin(pi/18) (triangle), as in Fig. 6."""
+    from paper_1603_08357_gb300 import percolation as P
+    pc = P.PC_EXACT["triangle"]
+    ps = np.linspace(pc - 0.03, pc + 0.03, 7)
+    curves = []
+    for Ls in (64, 128):
+        lat = L.make_instance(dict(kind="triangle", L=Ls, p=0.0, seed=0, periodic_y=False))
+        curves.append(P.Sampler(ctx, lat, *P.boundary_rows("triangle", Ls)).spanning_curve(ps, 1500, 77))
+    for R in curves:
+        assert np.all(np.diff(R) >= 0) and R[0] < 0.3 and R[-1] > 0.7
+    x, err = P.crossing(ps, curves[0], curves[1], 1500)
+    assert err is not None and 0 < err < 0.005
+    assert x is not None and abs(x - pc) < 0.01, x

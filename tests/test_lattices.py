@@ -139,3 +139,14 @@ def test_workload_sizes():
     specs = L.batched_mix_specs(64, seed=4)
     assert all(L.instance_size(s) <= 2 * 1024 * 1024 for s in specs)
     assert abs(L.PC_HONEYCOMB + L.PC_TRIANGLE - 1.0) < 1e-15     # duality of the two thresholds
+
+
+def test_crossing_interpolation():
+    from paper_1603_08357_gb300 import percolation as P
+    ps = np.array([0.1, 0.2, 0.3, 0.4, 0.5])
+    ra = np.array([0.0, 0.2, 0.4, 0.6, 1.0])
+    rb = np.array([0.0, 0.1, 0.4, 0.8, 1.0])     # cross exactly at 0.3, tie at both ends
+    assert P.crossing(ps, ra, rb)[0] == pytest.approx(0.3)
+    rb2 = np.array([0.0, 0.1, 0.3, 0.9, 1.0])     # d = 0, .1, .1, -.3, 0 -> crossing at 0.325
+    assert P.crossing(ps, ra, rb2)[0] == pytest.approx(0.325)
+    assert P.crossing(ps, ra, ra) == (None, None)
