@@ -163,18 +163,26 @@ def max_over_ranks(value: float, dist, device=None) -> float:
     return float(t.item())
 
 
-def algorithmic_bytes(n: int, nnz: int, q: int) -> dict:
+def algorithmic_bytes(n: int, nnz: int, q: int, input_kind: str = "csr", width: int = 0) -> dict:
     """Minimum bytes each step must move (each array read or written once).
 
-    init:     row_ptr 4(n+1) + col_idx 4 nnz + bit words 4 ceil(nnz/32) + labels 4n
-              + residual pairs 8q + chunk records 16 ceil(n/32)
+    init (csr):          row_ptr 4(n+1) + col_idx 4 nnz + bit words 4 ceil(nnz/32)
+                         + labels 4n + residual pairs 8q
+    init (random):       as csr without the bit words (bonds drawn on the device)
+    init (dense):        neighbour slots 4 width n + bit words 4 ceil(width n/32)
+                         + labels 4n + pairs 8q
+    init (dense-random): neighbour slots 4 width n + labels 4n + pairs 8q
     analysis: labels read 4n + write 4n (each of steps ii and iv)
-    reduce:   chunk records 16 ceil(n/32) + pairs 8q + two label reads 8q
+    reduce:   pairs 8q + two label reads 8q
     """
-    chunks = (n + 31) // 32
-    b_init = 4 * (n + 1) + 4 * nnz + 4 * ((nnz + 31) // 32) + 4 * n + 8 * q + 16 * chunks
+    if input_kind in ("dense", "dense-random"):
+        slots = width * n
+        b_in = 4 * slots + (4 * ((slots + 31) // 32) if input_kind == "dense" else 0)
+    else:
+        b_in = 4 * (n + 1) + 4 * nnz + (4 * ((nnz + 31) // 32) if input_kind == "csr" else 0)
+    b_init = b_in + 4 * n + 8 * q
     b_ana = 8 * n
-    b_red = 16 * chunks + 16 * q
+    b_red = 16 * q
     return {"init": b_init, "analysis_ii": b_ana, "reduce": b_red, "analysis_iv": b_ana,
             "path": b_init + 2 * b_ana + b_red}
 
@@ -246,10 +254,19 @@ def run_ours(args, rank, world, local):
     import paper_1603_08357_gb300 as ccl
 
     lat, desc = make_workload(args.config, rank)
+    kind = args.input
     rp = torch.from_numpy(lat.row_ptr).to(dev)
     ci = torch.from_numpy(lat.col_idx).to(dev)
     bits = torch.from_numpy(lat.open_bits.view(np.int32)).to(dev)
     labels = torch.empty(lat.n, dtype=torch.int32, device=dev)
+    width, h_nn, h_dbits = 0, None, None
+    if kind in ("dense", "dense-random"):
+        # the same graph and bond states as a dense strided neighbour list
+        width, h_nn, h_dbits = L.to_dense(lat)
+        d_nn = torch.from_numpy(h_nn).to(dev)
+        d_dbits = torch.from_numpy(h_dbits.view(np.int32)).to(dev)
+    seed_of = lambda k: (lat.seed * 1_000_003 + k) & (2**64 - 1)  # noqa: E731
+    step_no = [0]
     ctx = ccl.ccl_context_create(local)
     stream = torch.cuda.current_stream(dev)
     tuned = None
@@ -262,9 +279,17 @@ def run_ours(args, rank, world, local):
         ("pre_analysis", ccl.CCL_OPT_PRE_ANALYSIS), ("link_mode", ccl.CCL_OPT_LINK_MODE))}
 
     def step():
-        st = ccl.ccl_label(ctx, lat.n, lat.nnz, rp, ci, bits, labels, stream)
+        if kind == "csr":
+            st = ccl.ccl_label(ctx, lat.n, lat.nnz, rp, ci, bits, labels, stream)
+        elif kind == "dense":
+            st = ccl.ccl_label_dense(ctx, lat.n, width, d_nn, d_dbits, labels, stream)
+        elif kind == "random":       # a new realisation every step
+            st = ccl.ccl_label_random(ctx, lat.n, lat.nnz, rp, ci, seed_of(step_no[0]), lat.p, labels, stream)
+        else:
+            st = ccl.ccl_label_dense_random(ctx, lat.n, width, d_nn, seed_of(step_no[0]), lat.p, labels, stream)
+        step_no[0] += 1
         if st != ccl.CCL_OK:
-            raise ccl.CclError(st, "ccl_label")
+            raise ccl.CclError(st, kind)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -320,18 +345,39 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     ms_graph = g0.elapsed_time(g1) / args.steps
 
-    # end-to-end through the host-buffer entry point, pinned host memory
-    h_rp = torch.from_numpy(lat.row_ptr).pin_memory()
-    h_ci = torch.from_numpy(lat.col_idx).pin_memory()
-    h_bits = torch.from_numpy(lat.open_bits.view(np.int32)).pin_memory()
+    # end-to-end from pinned host memory: csr through the host-buffer entry
+    # point; the other inputs copy their arrays in, label, and copy labels out
+    last_seed = seed_of(step_no[0] - 1)
+    last_labels = labels.cpu().numpy()
     h_lab = torch.empty(lat.n, dtype=torch.int32).pin_memory()
     e_steps = max(1, min(args.steps, 10))
+    if kind == "csr":
+        h_rp = torch.from_numpy(lat.row_ptr).pin_memory()
+        h_ci = torch.from_numpy(lat.col_idx).pin_memory()
+        h_bits = torch.from_numpy(lat.open_bits.view(np.int32)).pin_memory()
+        h2d = 4 * (lat.n + 1) + 4 * lat.nnz + 4 * lat.open_bits.size
+        entry = "ccl_label_host (pinned host buffers)"
 
-    def e2e_step():
-        s = ccl.ccl_label_host(ctx, lat.n, lat.nnz, h_rp.data_ptr(), h_ci.data_ptr(),
-                               h_bits.data_ptr(), h_lab.data_ptr(), stream)
-        if s != ccl.CCL_OK:
-            raise ccl.CclError(s, "ccl_label_host")
+        def e2e_step():
+            s = ccl.ccl_label_host(ctx, lat.n, lat.nnz, h_rp.data_ptr(), h_ci.data_ptr(),
+                                   h_bits.data_ptr(), h_lab.data_ptr(), stream)
+            if s != ccl.CCL_OK:
+                raise ccl.CclError(s, "ccl_label_host")
+    else:
+        host_in = ([torch.from_numpy(lat.row_ptr), torch.from_numpy(lat.col_idx)] if kind == "random" else
+                   [torch.from_numpy(h_nn)] + ([torch.from_numpy(h_dbits.view(np.int32))] if kind == "dense" else []))
+        host_in = [t.pin_memory() for t in host_in]
+        dev_in = [rp, ci] if kind == "random" else ([d_nn] + ([d_dbits] if kind == "dense" else []))
+        h2d = sum(t.numel() * 4 for t in host_in)
+        entry = {"dense": "ccl_label_dense", "random": "ccl_label_random",
+                 "dense-random": "ccl_label_dense_random"}[kind] + " with pinned H2D/D2H copies"
+
+        def e2e_step():
+            for h, d in zip(host_in, dev_in):
+                d.copy_(h, non_blocking=True)
+            step()
+            h_lab.copy_(labels, non_blocking=True)
+            ccl.check(ccl.ccl_sync(ctx, stream), "e2e")
 
     for _ in range(2):
         e2e_step()
@@ -342,19 +388,26 @@ def run_ours(args, rank, world, local):
         e2e_step()
     e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / e_steps, dist, dev)
 
-    # sampled parity guard on the labels of the last step
+    # parity guard on the labels of the last timed step (full comparison in tests)
     import oracle
-    got = labels.cpu().numpy()
-    ok_sample = bool(np.array_equal(got, oracle.uf_label(lat))) if lat.n <= 60_000_000 else None
+    if lat.n > 60_000_000:
+        ok_sample = None
+    elif kind in ("random", "dense-random"):
+        import dataclasses
+        want = oracle.uf_label(dataclasses.replace(lat, open_bits=oracle.keyed_bits(lat, last_seed, lat.p)))
+        ok_sample = bool(np.array_equal(last_labels, want))
+    else:
+        ok_sample = bool(np.array_equal(last_labels, oracle.uf_label(lat)))
 
     if rank == 0:
         peak, peak_src = _peaks()
-        ab = algorithmic_bytes(lat.n, lat.nnz, q)
+        ab = algorithmic_bytes(lat.n, lat.nnz, q, kind, width)
         names = ["init", "analysis_ii", "reduce", "analysis_iv"]
         dom = max(range(4), key=lambda i: kern[i] if kern[i] > 0.005 else -1)
         dom_name = names[dom]
         achieved = ab[dom_name] / (kern[dom] / 1e3) / 1e9
-        traffic, scaled = _ncu_traffic(dom_name, args.config)
+        workload = args.config if kind == "csr" else f"{args.config}/{kind}"
+        traffic, scaled = _ncu_traffic(dom_name, workload)
         cpu = None
         if not args.no_cpu_baseline:
             v, reps, secs = oracle_time(lat, args.cpu_seconds)
@@ -371,7 +424,8 @@ def run_ours(args, rank, world, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
-            "config": {"workload": args.config, "desc": desc, "n_sites": lat.n, "nnz": lat.nnz,
+            "config": {"workload": workload, "desc": desc, "input": kind, "width": width or None,
+                       "n_sites": lat.n, "nnz": lat.nnz,
                        "residual_pairs": q, "options": opts, "autotune": tuned,
                        "l2": "inputs larger than L2 (no flush)" if lat.nnz * 4 > L2_BYTES
                        else "inputs L2-resident (no flush)",
@@ -386,9 +440,9 @@ def run_ours(args, rank, world, local):
                          "traffic_note": scaled},
             "cpu_baseline": cpu,
             "e2e": {"value": world * lat.n / (e_ms / 1e3), "unit": "sites/s",
-                    "h2d_bytes_per_step": 4 * (lat.n + 1) + 4 * lat.nnz + 4 * lat.open_bits.size,
+                    "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": 4 * lat.n, "ms_per_step": e_ms,
-                    "entry": "ccl_label_host (pinned host buffers)"},
+                    "entry": entry},
             "gpu_launches": args.steps * (4 if opts["pre_analysis"] else 3),
             "clocks": clk,
             "parity_last_step": ok_sample,
@@ -536,6 +590,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--input", choices=["csr", "dense", "random", "dense-random"], default="csr",
+                    help="single-instance configs: CSR with bit words (default), the dense strided "
+                         "neighbour list, or either with bonds drawn on the device")
     args = ap.parse_args()
     rank, world, local = _env_rank()
     if args.impl == "reference":

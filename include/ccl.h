@@ -145,6 +145,36 @@ CCL_API ccl_status ccl_label_random(ccl_context *ctx, int32_t n_sites, int64_t n
                                     void *stream);
 
 /*
+ * ccl_label_dense -- ccl_label on the dense strided nearest-neighbour list of
+ * Section 3: the list has `width` slots per site (the largest neighbour count
+ * of any site) and slot k of site i is nn[i + k * n_sites].
+ *   nn         device int32[n_sites * width]; a slot holds a site in
+ *              [0, n_sites) or -1 (empty: the site has fewer neighbours).
+ *              Any other value sets CCL_ERR_INDEX_OUT_OF_RANGE at ccl_sync.
+ *   open_bits  device uint32[ceil(n_sites * width / 32)]: slot e = i + k*n_sites
+ *              has its open bit at word e >> 5, bit e & 31.
+ *   labels     device int32[n_sites], written as by ccl_label.
+ * As for CSR input, the bond {i, j} is read from the slots of the larger site
+ * only, and a neighbour may appear in several slots (a multigraph).
+ * 0 <= width <= CCL_DENSE_MAX_WIDTH; width 0 labels every site by itself.
+ * The call uses n_sites * width queue slots of workspace (8 bytes each).
+ * Asynchronous on `stream`; replays a CUDA graph for repeated identical calls.
+ */
+#define CCL_DENSE_MAX_WIDTH 4096
+CCL_API ccl_status ccl_label_dense(ccl_context *ctx, int32_t n_sites, int32_t width, const int32_t *nn,
+                                   const uint32_t *open_bits, int32_t *labels, void *stream);
+
+/*
+ * ccl_label_dense_random -- ccl_label_dense with the bonds drawn on the
+ * device exactly as ccl_label_random draws them (bond {i, j}, i < j, keyed by
+ * i * 2^32 + j), so a dense list and a CSR list of the same graph give the
+ * same realisation for the same (seed, p). 0 <= p <= 1.
+ */
+CCL_API ccl_status ccl_label_dense_random(ccl_context *ctx, int32_t n_sites, int32_t width,
+                                          const int32_t *nn, uint64_t seed, double p, int32_t *labels,
+                                          void *stream);
+
+/*
  * ccl_label_host -- ccl_label on HOST arrays: copies the inputs to context
  * buffers, labels, copies the labels back and waits. Synchronous. Pinned
  * (page-locked) host memory gives the full copy bandwidth.

@@ -30,6 +30,8 @@ _lib = None
 
 PC_HONEYCOMB = 1.0 - 2.0 * math.sin(math.pi / 18.0)
 PC_TRIANGLE = 2.0 * math.sin(math.pi / 18.0)
+PC_SQUARE = 0.5                 # bond percolation, exact (Sykes & Essam 1964)
+PC_CUBIC = 0.2488126            # simple cubic bond percolation (Lorenz & Ziff 1998)
 
 
 def pc_bethe(z: int) -> float:
@@ -120,7 +122,7 @@ class Lattice:
 
 def _desc(kind: str, n: int, L=0, periodic_y=True, z=0, shells=0, perm=None, perm_inv=None):
     d = _Desc()
-    d.kind = {"honeycomb": 0, "triangle": 1, "cayley": 2}[kind]
+    d.kind = {"honeycomb": 0, "triangle": 1, "cayley": 2, "square": 3, "cubic": 4}[kind]
     d.L, d.periodic_y, d.z, d.shells, d.n = L, int(bool(periodic_y)), z, shells, n
     d.perm = perm.ctypes.data if perm is not None else None
     d.perm_inv = perm_inv.ctypes.data if perm_inv is not None else None
@@ -130,8 +132,10 @@ def _desc(kind: str, n: int, L=0, periodic_y=True, z=0, shells=0, perm=None, per
 def _nsites(kind, L=0, z=0, shells=0) -> int:
     if kind == "honeycomb":
         return 2 * L * L
-    if kind == "triangle":
+    if kind in ("triangle", "square"):
         return L * L
+    if kind == "cubic":
+        return L * L * L
     return int(_load().lat_cayley_nsites(z, shells))
 
 
@@ -184,6 +188,17 @@ def triangle(L: int, p: float, seed: int, periodic_y: bool = True, nthreads=None
     return _make("triangle", seed, p, nthreads, L=L, periodic_y=periodic_y)
 
 
+def square(L: int, p: float, seed: int, periodic_y: bool = True, nthreads=None) -> Lattice:
+    """Square-lattice bond percolation on L x L sites (coordination 4)."""
+    return _make("square", seed, p, nthreads, L=L, periodic_y=periodic_y)
+
+
+def cubic(L: int, p: float, seed: int, periodic_y: bool = True, nthreads=None) -> Lattice:
+    """Simple-cubic bond percolation on L^3 sites (coordination 6); with
+    periodic_y=False the z direction is open."""
+    return _make("cubic", seed, p, nthreads, L=L, periodic_y=periodic_y)
+
+
 def cayley(z: int, shells: int, p: float, seed: int, perm_seed: int | None = None,
            nthreads=None) -> Lattice:
     """Bethe-lattice (Cayley tree) bond percolation, coordination z, `shells` shells.
@@ -195,10 +210,13 @@ def cayley(z: int, shells: int, p: float, seed: int, perm_seed: int | None = Non
 
 
 def row_sites(lat: Lattice, y: int) -> np.ndarray:
-    """Sites whose cell row is y (honeycomb: both A and B of the cell)."""
+    """Sites whose cell row is y (honeycomb: both A and B of the cell; cubic:
+    the plane z = y)."""
     L = lat.meta["L"]
-    if lat.kind == "triangle":
+    if lat.kind in ("triangle", "square"):
         return np.arange(y * L, (y + 1) * L, dtype=np.int64)
+    if lat.kind == "cubic":
+        return np.arange(y * L * L, (y + 1) * L * L, dtype=np.int64)
     c = np.arange(y * L, (y + 1) * L, dtype=np.int64)
     return np.concatenate([2 * c, 2 * c + 1])
 
@@ -415,8 +433,44 @@ def make_instance(spec: dict, nthreads=None) -> Lattice:
         return honeycomb(spec["L"], spec["p"], spec["seed"], spec.get("periodic_y", True), nthreads)
     if kind == "triangle":
         return triangle(spec["L"], spec["p"], spec["seed"], spec.get("periodic_y", True), nthreads)
+    if kind == "square":
+        return square(spec["L"], spec["p"], spec["seed"], spec.get("periodic_y", True), nthreads)
+    if kind == "cubic":
+        return cubic(spec["L"], spec["p"], spec["seed"], spec.get("periodic_y", True), nthreads)
     return cayley(spec["z"], spec["shells"], spec["p"], spec["seed"], spec.get("perm_seed"), nthreads)
 
 
 def instance_size(spec: dict) -> int:
     return _nsites(spec["kind"], spec.get("L", 0), spec.get("z", 0), spec.get("shells", 0))
+
+
+def to_dense(lat: Lattice, width: int | None = None, slot_seed: int | None = None):
+    """The dense strided neighbour list of the same graph and bond states:
+    returns (width, nn, bits) with nn int32[width * n] (slot k of site i at
+    nn[i + k*n], -1 where empty) and bits uint32[ceil(width*n/32)] (slot e's
+    state at bit e). width defaults to the largest degree; with slot_seed
+    each row's entries go to seeded random distinct slots (empty slots then
+    sit between used ones), else to slots 0..deg-1 in CSR order."""
+    n = lat.n
+    rp = np.asarray(lat.row_ptr, np.int64)
+    deg = np.diff(rp)
+    W = int(deg.max()) if n and lat.nnz else 0
+    width = W if width is None else int(width)
+    if width < W:
+        raise ValueError("width below the largest degree")
+    nn = np.full(width * n, -1, np.int32)
+    bits = np.zeros(max(1, (width * n + 31) // 32), np.uint32)
+    if lat.nnz == 0:
+        return width, nn, bits
+    row = np.repeat(np.arange(n, dtype=np.int64), deg)
+    k = np.arange(lat.nnz, dtype=np.int64) - rp[row]
+    if slot_seed is not None:
+        rng = np.random.default_rng(slot_seed)
+        keys = rng.random((n, width)).argsort(axis=1)      # a random slot order per row
+        k = keys[row, k]
+    slot = row + k * n
+    nn[slot] = np.asarray(lat.col_idx, np.int32)
+    on = unpack_bits(lat.open_bits, lat.nnz).astype(bool)
+    s_on = slot[on]
+    np.bitwise_or.at(bits, s_on >> 5, (np.uint32(1) << (s_on & 31).astype(np.uint32)))
+    return width, nn, bits

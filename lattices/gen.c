@@ -32,8 +32,15 @@
  *                 by shell from the centre ("standard position"). The bond
  *                 between a site s > 0 and its parent has id s - 1.
  *                 "Random position" stores standard site s at index perm[s].
- * x is always periodic; y is periodic unless periodic_y == 0, in which case
- * bonds that would wrap in y are absent (the spanning direction).
+ *   square(L):    L x L sites i = y*L + x (the 2D lattice the four steps were
+ *                 first written for). Bond 2i : (x,y) - (x+1,y)
+ *                                     Bond 2i+1 : (x,y) - (x,y+1)
+ *   cubic(L):     L^3 sites i = (z*L + y)*L + x (simple cubic).
+ *                 Bond 3i + d : i - (its neighbour one step up along axis d,
+ *                 d = 0: x, 1: y, 2: z)
+ * x is always periodic; y (z for cubic) is periodic unless periodic_y == 0,
+ * in which case bonds that would wrap in that direction are absent (the
+ * spanning direction). cubic's y is always periodic.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -57,7 +64,7 @@ int lat_bond_open(uint64_t seed, uint64_t bond, double p) {
     return (double)(h >> 11) * 0x1.0p-53 < p;
 }
 
-enum { LAT_HONEYCOMB = 0, LAT_TRIANGLE = 1, LAT_CAYLEY = 2 };
+enum { LAT_HONEYCOMB = 0, LAT_TRIANGLE = 1, LAT_CAYLEY = 2, LAT_SQUARE = 3, LAT_CUBIC = 4 };
 
 typedef struct {
     int32_t kind;
@@ -147,6 +154,35 @@ static int neighbors(const lat_desc *d, int64_t i, int64_t *nb, int64_t *bond) {
         nb[cnt] = y * L + xm; bond[cnt] = 3 * (y * L + xm); ++cnt;
         if (dn) { nb[cnt] = ym * L + x;  bond[cnt] = 3 * (ym * L + x) + 1; ++cnt; }
         if (dn) { nb[cnt] = ym * L + xm; bond[cnt] = 3 * (ym * L + xm) + 2; ++cnt; }
+        return cnt;
+    }
+    if (d->kind == LAT_SQUARE) {
+        int64_t L = d->L, x = i % L, y = i / L;
+        int cnt = 0;
+        nb[cnt] = y * L + (x + 1) % L; bond[cnt] = 2 * i; ++cnt;
+        if (d->periodic_y || y < L - 1) { nb[cnt] = ((y + 1) % L) * L + x; bond[cnt] = 2 * i + 1; ++cnt; }
+        int64_t l = y * L + (x + L - 1) % L;
+        nb[cnt] = l; bond[cnt] = 2 * l; ++cnt;
+        if (d->periodic_y || y > 0) {
+            int64_t dn = ((y + L - 1) % L) * L + x;
+            nb[cnt] = dn; bond[cnt] = 2 * dn + 1; ++cnt;
+        }
+        return cnt;
+    }
+    if (d->kind == LAT_CUBIC) {
+        int64_t L = d->L, x = i % L, y = (i / L) % L, z = i / (L * L);
+        int64_t c[3] = {x, y, z}, stride[3] = {1, L, L * L};
+        int cnt = 0;
+        for (int a = 0; a < 3; ++a) {       /* upward neighbours: bond 3i + a */
+            if (a == 2 && !d->periodic_y && z == L - 1) continue;
+            int64_t j = i + (((c[a] + 1) % L) - c[a]) * stride[a];
+            nb[cnt] = j; bond[cnt] = 3 * i + a; ++cnt;
+        }
+        for (int a = 0; a < 3; ++a) {       /* downward neighbours: their bond 3j + a */
+            if (a == 2 && !d->periodic_y && z == 0) continue;
+            int64_t j = i + (((c[a] + L - 1) % L) - c[a]) * stride[a];
+            nb[cnt] = j; bond[cnt] = 3 * j + a; ++cnt;
+        }
         return cnt;
     }
     /* Cayley tree, optionally stored under a permutation */

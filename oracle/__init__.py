@@ -10,7 +10,8 @@ number of each site's cluster of open bonds, where the bond {i, j} is read
 from row max(i, j). Three independent C routines (``ccl_oracle.c``): weighted
 union-find, breadth-first search, and the four steps of Section 3 run on one
 core. ``stats`` holds the Section 4 measurements made on labels (spanning,
-cluster counts, the centre cluster of a Bethe lattice).
+cluster counts, the centre cluster of a Bethe lattice). ``dense_to_csr``
+reads the dense strided neighbour list of Section 3 back into CSR rows.
 
 Parity pins (tests/test_oracle_*.py): brute force over every bond mask of
 graphs with at most 12 bonds against scipy's connected components; a worked
@@ -138,6 +139,59 @@ def keyed_bits(lat, seed: int, p: float) -> np.ndarray:
     _check(_load().oracle_keyed_bits(lat.n, lat.nnz, _ptr(rp), _ptr(ci), seed & (2**64 - 1), float(p),
                                      _ptr(bits)))
     return bits
+
+
+class _Csr:
+    def __init__(self, n, row_ptr, col_idx, open_bits):
+        self.n, self.nnz = n, int(col_idx.size)
+        self.row_ptr, self.col_idx, self.open_bits = row_ptr, col_idx, open_bits
+
+
+def dense_to_csr(n: int, width: int, nn: np.ndarray, bits: np.ndarray | None = None):
+    """The graph of a dense strided neighbour list (Section 3: slot k of site
+    i is nn[i + k*n], -1 = empty) as CSR rows: row i lists the non-empty slots
+    of site i in slot order, each with the open bit of its slot (bit i + k*n).
+    Raises ValueError for a slot outside [-1, n)."""
+    nn = np.asarray(nn, np.int64).reshape(width, n) if width else np.zeros((0, n), np.int64)
+    if nn.size and (nn.min() < -1 or nn.max() >= n):
+        raise ValueError("dense neighbour list: slot out of range")
+    used = (nn >= 0).T                                   # [n, width]: row i, slot k
+    rows, ks = np.nonzero(used)                          # row-major: rows ascending, k ascending
+    row_ptr = np.zeros(n + 1, np.int32)
+    np.cumsum(used.sum(axis=1), out=row_ptr[1:])
+    col_idx = nn[ks, rows].astype(np.int32)
+    slot = rows + ks * n
+    if bits is None:
+        open_bits = np.zeros(max(1, (col_idx.size + 31) // 32), np.uint32)
+    else:
+        b = np.asarray(bits, np.uint32)
+        on = ((b[slot >> 5] >> (slot & 31).astype(np.uint32)) & 1).astype(np.uint8)
+        open_bits = np.zeros(max(1, (col_idx.size + 31) // 32) * 4, np.uint8)
+        packed = np.packbits(on, bitorder="little")
+        open_bits[:packed.size] = packed
+        open_bits = open_bits.view("<u4").astype(np.uint32)
+    return _Csr(n, row_ptr, col_idx, open_bits)
+
+
+def dense_uf_label(n: int, width: int, nn: np.ndarray, bits: np.ndarray) -> np.ndarray:
+    """Canonical labels of a dense strided neighbour list (union-find on the
+    same graph as CSR rows)."""
+    return uf_label(dense_to_csr(n, width, nn, bits))
+
+
+def dense_keyed_bits(n: int, width: int, nn: np.ndarray, seed: int, p: float) -> np.ndarray:
+    """Slot bits of realisation (seed, p): each non-empty slot gets the state
+    ``keyed_bits`` gives its bond {min(i, j), max(i, j)}."""
+    g = dense_to_csr(n, width, nn)
+    kb = keyed_bits(g, seed, p)
+    nnv = np.asarray(nn, np.int64).reshape(width, n) if width else np.zeros((0, n), np.int64)
+    rows, ks = np.nonzero((nnv >= 0).T)
+    slot = rows + ks * n
+    on = ((kb[np.arange(g.nnz) >> 5] >> (np.arange(g.nnz) & 31).astype(np.uint32)) & 1).astype(bool)
+    out = np.zeros(max(1, (width * n + 31) // 32), np.uint32)
+    s_on = slot[on]
+    np.bitwise_or.at(out, s_on >> 5, np.uint32(1) << (s_on & 31).astype(np.uint32))
+    return out
 
 
 def uf_label_batched(batch, k0: int = 0, k1: int | None = None) -> np.ndarray:

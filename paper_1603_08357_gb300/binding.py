@@ -90,6 +90,8 @@ def _load() -> ctypes.CDLL:
         "ccl_label_batched": (C, [P, I32, P, P, P, P, P, P, P]),
         "ccl_label_host": (C, [P, I32, I64, P, P, P, P, P]),
         "ccl_label_random": (C, [P, I32, I64, P, P, ctypes.c_uint64, ctypes.c_double, P, P]),
+        "ccl_label_dense": (C, [P, I32, I32, P, P, P, P]),
+        "ccl_label_dense_random": (C, [P, I32, I32, P, ctypes.c_uint64, ctypes.c_double, P, P]),
         "ccl_label_noalloc": (C, [I32, I64, P, P, P, P, P]),
         "ccl_reserve": (C, [P, I64, I64, I64]),
         "ccl_relabel": (C, [P, I32, P, P, P, P, P]),
@@ -274,6 +276,22 @@ def ccl_label_random(ctx, n_sites: int, nnz: int, row_ptr, col_idx, seed: int, p
     return _lib.ccl_label_random(ctx, int(n_sites), int(nnz), _dev_ptr(row_ptr, "row_ptr", _i32()),
                                  _dev_ptr(col_idx, "col_idx", _i32()), ctypes.c_uint64(seed & (2**64 - 1)),
                                  float(p), _dev_ptr(labels, "labels", _i32()), _stream(stream))
+
+
+CCL_DENSE_MAX_WIDTH = 4096
+
+
+def ccl_label_dense(ctx, n_sites: int, width: int, nn, open_bits, labels, stream=None) -> int:
+    return _lib.ccl_label_dense(ctx, int(n_sites), int(width), _dev_ptr(nn, "nn", _i32()),
+                                _dev_ptr(open_bits, "open_bits", _bits_dtypes()),
+                                _dev_ptr(labels, "labels", _i32()), _stream(stream))
+
+
+def ccl_label_dense_random(ctx, n_sites: int, width: int, nn, seed: int, p: float, labels,
+                           stream=None) -> int:
+    return _lib.ccl_label_dense_random(ctx, int(n_sites), int(width), _dev_ptr(nn, "nn", _i32()),
+                                       ctypes.c_uint64(seed & (2**64 - 1)), float(p),
+                                       _dev_ptr(labels, "labels", _i32()), _stream(stream))
 
 
 def ccl_label_host(ctx, n_sites: int, nnz: int, row_ptr, col_idx, open_bits, labels,

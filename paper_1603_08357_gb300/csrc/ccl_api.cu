@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "ccl_device.cuh"
+#include "ccl_dense.cuh"
 #include "ccl_stats.cuh"
 
 using namespace ccl;
@@ -35,6 +36,9 @@ struct GraphEntry {
     int32_t K = 0;
     int64_t n_chunks = 0;
     const void *row_ptr = nullptr, *col_idx = nullptr, *bits = nullptr;
+    int32_t dense = 0;               // dense neighbour-list call
+    const void *nn = nullptr;
+    int64_t nn_width = 0;
     void *labels = nullptr;
     uint64_t shape_hash = 0;
     Inst one{};                      // the instance (single path), compared exactly
@@ -139,6 +143,8 @@ int blocks_per_sm(ccl_context *ctx, int kernel_id, int threads) {
         case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_reduce<false>, threads, 0); break;
         case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_reduce<true>, threads, 0); break;
         case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init<false, true>, kInitThreads, kInitSmem); break;
+        case 7: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init_dense<false>, kDenseThreads, 0); break;
+        case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init_dense<true>, kDenseThreads, 0); break;
         default: break;
     }
     if (e != cudaSuccess || nb < 1) { (void)cudaGetLastError(); nb = 1; }
@@ -157,8 +163,8 @@ int64_t grid_for(ccl_context *ctx, int kernel_id, const TuneChoice &tc, int64_t 
 
 // step (i): fixed CTA shape; CTA b takes the band of tiles [b*per, (b+1)*per),
 // so launch just enough CTAs for every band to be non-empty
-int64_t grid_init(ccl_context *ctx, bool batched, int64_t n_tiles) {
-    const int per_sm = blocks_per_sm(ctx, batched ? 1 : 0, kInitThreads);
+int64_t grid_init(ccl_context *ctx, int kernel_id, int threads, int64_t n_tiles) {
+    const int per_sm = blocks_per_sm(ctx, kernel_id, threads);
     int64_t g = std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * per_sm, n_tiles));
     g = std::min<int64_t>(g, kMaxBands);
     const int64_t per = (n_tiles + g - 1) / g;
@@ -216,15 +222,21 @@ ccl_status enqueue_steps(ccl_context *ctx, const Params &P0, bool batched, const
     const int T = tc.threads;
     const int64_t warps_chunks = (P0.n_chunks + kAnaChunks - 1) / kAnaChunks;
     Params P = P0;
-    const int64_t g_init = grid_init(ctx, batched, P.n_tiles);
+    const bool dense = P.dense != 0;
+    const bool gen = P.gen_thr != kNoGen;
+    const int64_t g_init = dense ? grid_init(ctx, gen ? 8 : 7, kDenseThreads, P.n_tiles)
+                                 : grid_init(ctx, batched ? 1 : (gen ? 6 : 0), kInitThreads, P.n_tiles);
     P.n_bands = (int32_t)g_init;
     const int64_t g_red = (int64_t)ctx->num_sms * blocks_per_sm(ctx, batched ? 5 : 4, 256);
     CCL_CUDA(cudaMemsetAsync(P.counters, 0, 4 * sizeof(unsigned long long), s));
     CCL_CUDA(cudaMemsetAsync(P.band, 0, (size_t)g_init * sizeof(BandRec), s));
     if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[0], s));
-    if (batched) {
+    if (dense) {
+        if (gen) k_init_dense<true><<<(unsigned)g_init, kDenseThreads, 0, s>>>(P);
+        else k_init_dense<false><<<(unsigned)g_init, kDenseThreads, 0, s>>>(P);
+    } else if (batched) {
         k_init<true><<<(unsigned)g_init, kInitThreads, kInitSmem, s>>>(P);
-    } else if (P.gen_thr != kNoGen) {
+    } else if (gen) {
         k_init<false, true><<<(unsigned)g_init, kInitThreads, kInitSmem, s>>>(P);
     } else {
         k_init<false><<<(unsigned)g_init, kInitThreads, kInitSmem, s>>>(P);
@@ -263,6 +275,7 @@ GraphEntry *find_graph(ccl_context *ctx, const GraphEntry &key) {
     for (auto &g : ctx->graphs) {
         if (g.K == key.K && g.n_chunks == key.n_chunks && g.row_ptr == key.row_ptr &&
             g.col_idx == key.col_idx && g.bits == key.bits && g.labels == key.labels &&
+            g.dense == key.dense && g.nn == key.nn && g.nn_width == key.nn_width &&
             g.shape_hash == key.shape_hash && same_choice(g.tc, key.tc) &&
             memcmp(&g.one, &key.one, sizeof(Inst)) == 0 && g.offsets == key.offsets)
             return &g;
@@ -305,8 +318,9 @@ bool stream_capturing(cudaStream_t s) {
 ccl_status run(ccl_context *ctx, Params P, bool batched, const TuneChoice &tc, cudaStream_t s,
                const std::vector<Inst> *table, uint64_t shape_hash, bool allow_graph = true,
                const std::vector<int64_t> *offsets = nullptr) {
-    for (int kid = 0; kid < 7; ++kid)
-        (void)blocks_per_sm(ctx, kid, (kid < 2 || kid == 6) ? kInitThreads : (kid >= 4 ? 256 : tc.threads));
+    for (int kid = 0; kid < 9; ++kid)
+        (void)blocks_per_sm(ctx, kid, kid >= 7 ? kDenseThreads
+                                               : (kid < 2 || kid == 6) ? kInitThreads : (kid >= 4 ? 256 : tc.threads));
     ctx->last.used_graph = 0;
     const bool capturing = stream_capturing(s);
     if (ctx->profile || !ctx->use_graphs || capturing || !allow_graph) {
@@ -355,6 +369,9 @@ ccl_status run(ccl_context *ctx, Params P, bool batched, const TuneChoice &tc, c
     key.col_idx = batched ? (const void *)(*table)[0].col_idx : P.one.col_idx;
     key.bits = batched ? (const void *)(*table)[0].bits : P.one.bits;
     key.labels = batched ? (void *)(*table)[0].labels : P.one.labels;
+    key.dense = P.dense;
+    key.nn = P.nn;
+    key.nn_width = P.nn_width;
     key.shape_hash = shape_hash;
     key.tc = tc;
     if (!batched) key.one = P.one;
@@ -450,6 +467,40 @@ ccl_status label_single(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t 
     }
     // the graph key covers every field of the instance (sizes included)
     return run(ctx, P, false, tc, s, nullptr, fnv1a(&P.one, sizeof(Inst)));
+}
+
+// Dense strided neighbour list: step (i) reads nn[i + k*n] (k < width) in
+// place of a CSR row; the queue has n*width slots.
+ccl_status label_dense(ccl_context *ctx, int32_t n, int32_t width, const int32_t *nn, const uint32_t *bits,
+                       int32_t *labels, cudaStream_t s, const TuneChoice &tc, uint64_t gen_seed = 0,
+                       uint64_t gen_thr = kNoGen) {
+    const int64_t slots = (int64_t)n * width;
+    ccl_status st = ensure_workspace(ctx, slots, false);
+    if (st != CCL_OK) return st;
+    Params P = base_params(ctx, tc);
+    P.K = 1;
+    P.n_chunks = ((int64_t)n + kChunk - 1) / kChunk;
+    P.n_tiles = ((int64_t)n + kTileSites - 1) / kTileSites;
+    P.dense = 1;
+    P.nn = nn;
+    P.nn_width = width;
+    P.one.bits = bits;
+    P.one.labels = labels;
+    P.one.n = n;
+    ctx->last.n_sites = n;
+    ctx->last.nnz = slots;
+    ctx->last.n_inst = 1;
+    if (gen_thr != kNoGen) {
+        P.gen_seed = gen_seed;
+        P.gen_thr = gen_thr;
+        return run(ctx, P, false, tc, s, nullptr, 0, false);
+    }
+    return run(ctx, P, false, tc, s, nullptr, fnv1a(&P.one, sizeof(Inst)) ^ (uint64_t)width);
+}
+
+// threshold of "(output >> 11) * 2^-53 < p": the smallest integer >= p * 2^53
+uint64_t gen_threshold(double p) {
+    return (uint64_t)std::ceil(p * 9007199254740992.0);
 }
 
 }  // namespace
@@ -705,11 +756,41 @@ ccl_status ccl_label_random(ccl_context *ctx, int32_t n, int64_t nnz, const int3
     if (st != CCL_OK || n == 0) return st;
     if (!(p >= 0.0 && p <= 1.0)) return CCL_ERR_INVALID_ARGUMENT;
     // open iff (output >> 11) * 2^-53 < p  <=>  (output >> 11) < ceil(p * 2^53)
-    const double scaled = std::ceil(p * 9007199254740992.0);
-    const uint64_t thr = (uint64_t)scaled;
+    const uint64_t thr = gen_threshold(p);
     DeviceGuard guard(ctx->device);
     const TuneChoice tc = choice_for(ctx, n, nnz);
     return label_single(ctx, n, nnz, row_ptr, col_idx, nullptr, labels, (cudaStream_t)stream, tc, seed, thr);
+}
+
+namespace {
+ccl_status check_dense_args(ccl_context *ctx, int32_t n, int32_t width, const int32_t *nn, const void *bits,
+                            const int32_t *labels) {
+    if (!ctx || n < 0 || width < 0 || width > CCL_DENSE_MAX_WIDTH) return CCL_ERR_INVALID_ARGUMENT;
+    if (n == 0) return CCL_OK;
+    if (!labels || (width > 0 && (!nn || !bits))) return CCL_ERR_INVALID_ARGUMENT;
+    return CCL_OK;
+}
+}  // namespace
+
+ccl_status ccl_label_dense(ccl_context *ctx, int32_t n, int32_t width, const int32_t *nn,
+                           const uint32_t *open_bits, int32_t *labels, void *stream) {
+    ccl_status st = check_dense_args(ctx, n, width, nn, open_bits, labels);
+    if (st != CCL_OK || n == 0) return st;
+    DeviceGuard guard(ctx->device);
+    const TuneChoice tc = choice_for(ctx, n, (int64_t)n * width);
+    return label_dense(ctx, n, width, width ? nn : nullptr, width ? open_bits : nullptr, labels,
+                       (cudaStream_t)stream, tc);
+}
+
+ccl_status ccl_label_dense_random(ccl_context *ctx, int32_t n, int32_t width, const int32_t *nn,
+                                  uint64_t seed, double p, int32_t *labels, void *stream) {
+    ccl_status st = check_dense_args(ctx, n, width, nn, (const void *)1, labels);
+    if (st != CCL_OK || n == 0) return st;
+    if (!(p >= 0.0 && p <= 1.0)) return CCL_ERR_INVALID_ARGUMENT;
+    DeviceGuard guard(ctx->device);
+    const TuneChoice tc = choice_for(ctx, n, (int64_t)n * width);
+    return label_dense(ctx, n, width, width ? nn : nullptr, nullptr, labels, (cudaStream_t)stream, tc, seed,
+                       gen_threshold(p));
 }
 
 namespace {

@@ -76,13 +76,15 @@ struct Params {
     int64_t n_chunks;          // over all instances
     int64_t n_tiles;           // over all instances
     int32_t n_bands;           // CTAs of step (i)
-    int32_t pad_;
+    int32_t dense;             // 1: step (i) reads the dense neighbour list nn
     BandRec *band;             // [n_bands]
     int2 *q;                   // residual pairs (i, j); slots indexed by global CSR entry
     int32_t *qk;               // instance of each pair (K > 1 only)
     int64_t q_cap;             // slots of q (and qk)
     uint64_t gen_seed;         // bonds drawn on the device: SplitMix64 state ...
     uint64_t gen_thr;          // ... and threshold (bond open iff output >> 11 < gen_thr)
+    const int32_t *nn;         // dense neighbour list (slot k of site i at nn[i + k*n]), or null
+    int64_t nn_width;          // slots per site of the dense list
     unsigned *err;
     unsigned long long *counters;   // [0] residual pairs
 };

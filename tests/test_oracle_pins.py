@@ -10,6 +10,7 @@
 * crossings of the spanning probability near p_c = 1 - 2 sin(pi/18)
   (honeycomb) and 2 sin(pi/18) (triangle), Section 4, Figs. 5-6.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -265,3 +266,86 @@ def test_sequential_and_spanning_by_hand():
     assert stats.spanning_label(lab, np.array([1, 2]), np.array([5, 4])) == 0
     assert stats.spanning_label(lab, np.array([2]), np.array([3, 4])) == 2
     assert stats.spanning_label(lab, np.array([4]), np.array([0, 2])) == -1
+
+
+# ---- dense strided neighbour lists (Section 3) and the square / cubic lattices
+
+def _dense_cases():
+    yield L.triangle(33, L.PC_TRIANGLE, 3)
+    yield L.honeycomb(20, 0.7, 4, periodic_y=False)
+    yield L.cayley(3, 9, 0.6, 5, perm_seed=2)
+    yield L.square(30, 0.5, 6)
+    yield L.cubic(9, 0.3, 7, periodic_y=False)
+    yield L.random_graph(700, 1500, 8)
+
+
+@pytest.mark.parametrize("slot_seed,extra", [(None, 0), (3, 0), (4, 5)])
+def test_dense_oracle_equals_csr_oracle(slot_seed, extra):
+    for lat in _dense_cases():
+        W0 = int(np.diff(lat.row_ptr).max())
+        W, nn, bits = L.to_dense(lat, W0 + extra, slot_seed)
+        assert np.array_equal(oracle.dense_uf_label(lat.n, W, nn, bits), oracle.uf_label(lat))
+        assert np.array_equal(oracle.dense_uf_label(lat.n, W, nn, bits), oracle.bfs_label(lat))
+
+
+def test_dense_by_hand():
+    # 4 sites, width 2: 0-1 open, 1-2 closed, 2-3 open, 3-0 open (ring with one gap)
+    #   slot 0 of each site: its clockwise neighbour, slot 1: anticlockwise
+    n, W = 4, 2
+    nn = np.array([1, 2, 3, 0,  3, 0, 1, 2], np.int32)
+    state = {(0, 1): 1, (1, 2): 0, (2, 3): 1, (0, 3): 1}
+    bits = np.zeros(1, np.uint32)
+    for e in range(8):
+        i, j = e % n, int(nn[e])
+        if state[(min(i, j), max(i, j))]:
+            bits[0] |= np.uint32(1 << e)
+    assert oracle.dense_uf_label(n, W, nn, bits).tolist() == [0, 0, 0, 0]
+    bits2 = bits & ~np.uint32((1 << 3) | (1 << 4))       # close 3-0 in both slots
+    assert oracle.dense_uf_label(n, W, nn, bits2).tolist() == [0, 0, 2, 2]
+    with pytest.raises(ValueError):
+        oracle.dense_to_csr(n, W, np.array([1, 2, 3, 4, -1, -1, -1, -1]))
+
+
+def test_dense_keyed_bits_match_csr():
+    lat = L.triangle(17, 0.3, 1)
+    W, nn, _ = L.to_dense(lat, 8, 5)
+    want = oracle.uf_label(dataclasses.replace(lat, open_bits=oracle.keyed_bits(lat, 123, 0.4)))
+    assert np.array_equal(oracle.dense_uf_label(lat.n, W, nn, oracle.dense_keyed_bits(lat.n, W, nn, 123, 0.4)),
+                          want)
+
+
+def test_square_and_cubic_structure():
+    for lat, z in ((L.square(12, 1.0, 1), 4), (L.cubic(6, 1.0, 1), 6)):
+        deg = np.diff(lat.row_ptr)
+        assert np.all(deg == z)
+        A = sp.csr_matrix((np.ones(lat.nnz), lat.col_idx, lat.row_ptr), shape=(lat.n, lat.n))
+        assert (A != A.T).nnz == 0
+        assert np.all(oracle.uf_label(lat) == 0)
+    assert L.cubic(6, 1.0, 1).nnz == 6 * 6 ** 3
+    assert L.square(10, 1.0, 1, periodic_y=False).nnz == 4 * 100 - 2 * 10    # no wrap in y
+    assert L.cubic(5, 1.0, 1, periodic_y=False).nnz == 6 * 125 - 2 * 25       # no wrap in z
+    # every open bond beyond a spanning forest closes a cycle: C >= N - open bonds
+    for lat in (L.square(40, 0.3, 2), L.cubic(10, 0.2, 3)):
+        lab = oracle.uf_label(lat)
+        assert stats.n_clusters(lab) >= lat.n - lat.n_open_bonds
+
+
+def test_square_crossing_near_half():
+    """Spanning curves of two sizes cross near the exact square-lattice
+    bond threshold 1/2."""
+    ps = [0.44, 0.47, 0.5, 0.53, 0.56]
+    R = {}
+    for Ls in (16, 48):
+        R[Ls] = []
+        for p in ps:
+            hits = 0
+            for s in range(300):
+                lat = L.square(Ls, p, 1000 * Ls + s, periodic_y=False)
+                hits += stats.spanning_label(oracle.uf_label(lat), L.row_sites(lat, 0),
+                                             L.row_sites(lat, Ls - 1)) >= 0
+            R[Ls].append(hits / 300)
+    d = np.array(R[16]) - np.array(R[48])
+    assert d[0] > 0 and d[-1] < 0
+    k = int(np.flatnonzero(np.diff(np.sign(d)) != 0)[0])
+    x = ps[k] + (ps[k + 1] - ps[k]) * d[k] / (d[k] - d[k + 1])
+    assert abs(x - 0.5) < 0.03, (x, R)
