@@ -212,31 +212,55 @@ def _ncu_traffic(kernel: str, workload: str):
 
 # ----------------------------------------------------------------------------
 
+def _reference_sample(config: str):
+    """The instances one reference step labels: the whole instance for the
+    single-instance configs; for the batched and served mixes a bounded
+    sample of their instances (the first ones of the seeded stream)."""
+    if config == "batched":
+        specs = L.batched_mix_specs(4096, seed=4)[:24]
+        return [L.make_instance(sp) for sp in specs], "batched mix, first 24 instances"
+    if config == "served":
+        specs = L.served_specs(2000, seed=5)[:24]
+        return [L.make_instance(sp) for sp in specs], "served stream, first 24 requests"
+    lat, desc = make_workload(config, 0)
+    return [lat], desc
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    lat, desc = make_workload(args.config, 0)
-    import oracle  # noqa: F401
+    lats, desc = _reference_sample(args.config)
+    lat = lats[0]
+    import oracle
+    n_step = sum(x.n for x in lats)
+
+    def one_step():
+        for x in lats:
+            oracle.uf_label(x)
+
     per_step = []
     for _ in range(args.warmup):
-        oracle_time(lat, 0.0)
+        one_step()
     t_all = time.perf_counter()
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle_time(lat, 0.0)
+        one_step()
         per_step.append(time.perf_counter() - t0)
     wall = time.perf_counter() - t_all
     ms = 1e3 * wall / args.steps
-    value = lat.n / (ms / 1e3)
+    value = n_step / (ms / 1e3)
     line = {
-        "impl": "reference", "metric": "sites labeled/s", "value": value, "unit": "sites/s",
+        "impl": "reference", "value": value, "unit": "sites/s",
+        "metric": {"batched": "sites labeled/s (batched)", "served": "sites labeled/s (served)"}.get(
+            args.config, "sites labeled/s"),
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": args.config, "desc": desc, "n_sites": lat.n, "nnz": lat.nnz,
+        "config": {"workload": args.config, "desc": desc, "n_sites": n_step,
+                   "nnz": sum(x.nnz for x in lats),
                    "l2": "inputs larger than L2 (no flush)" if lat.nnz * 4 > L2_BYTES else "L2-resident"},
         "cpu_baseline": {"value": value, "unit": "sites/s", "cores": 1, "kind": "oracle",
-                         "sample": f"union-find oracle over the full instance ({lat.n} sites), "
+                         "sample": f"union-find oracle over {desc} ({n_step} sites), "
                                    f"one pass per step, 1 thread"},
         "e2e": {"value": value, "unit": "sites/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -545,10 +569,11 @@ def run_batched(args, rank, world, local):
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
+            inst = [b.instance(k) for k in sample]      # built before the clock starts
             t0, done, sites = time.perf_counter(), 0, 0
-            for k in sample:
-                oracle.uf_label(b.instance(k))
-                sites += int(so[k + 1] - so[k])
+            for lat in inst:
+                oracle.uf_label(lat)
+                sites += lat.n
                 done += 1
                 if time.perf_counter() - t0 > args.cpu_seconds:
                     break
@@ -578,18 +603,166 @@ def run_batched(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def run_served(args, rank, world, local):
+    """The served workload: requests of log-uniform size (1e3..1e7 sites, the
+    three lattice types at p_c) through the request loop (ccl_server_*),
+    host arrays in, labels back on the host. First the capacity with a
+    bounded number of requests in flight (closed loop), then Poisson arrivals
+    at a fraction of that capacity (open loop) for the latency percentiles.
+    Requests repeat a pool of distinct pre-generated instances (the whole
+    stream would not fit in host memory)."""
+    import torch
+    import oracle
+    torch.cuda.set_device(local)
+    import paper_1603_08357_gb300 as ccl
+    t_gen = time.perf_counter()
+    specs = L.served_specs(args.requests, seed=5 + 1000 * rank)
+    pool = [L.make_instance(sp) for sp in specs[:args.pool]]
+    t_gen = time.perf_counter() - t_gen
+    req = [pool[r % len(pool)] for r in range(args.requests)]
+    mean_sites = float(np.mean([lat.n for lat in req]))
+    out_bufs = {id(lat): np.empty(lat.n, np.int32) for lat in pool}
+
+    def submit(srv, lat):
+        while True:
+            st, t = ccl.ccl_server_submit(srv, lat.n, lat.nnz, lat.row_ptr, lat.col_idx, lat.open_bits)
+            if st == ccl.CCL_OK:
+                return t
+            if st != ccl.CCL_ERR_REJECTED:
+                raise ccl.CclError(st, "ccl_server_submit")
+            time.sleep(0.0005)
+
+    def drain(srv, tickets, lats, keep=None):
+        for k, (t, lat) in enumerate(zip(tickets, lats)):
+            buf = out_bufs[id(lat)] if keep is None or k not in keep else np.empty(lat.n, np.int32)
+            ccl.check(ccl.ccl_server_wait(srv, t, buf, 600_000), "ccl_server_wait")
+            if keep is not None and k in keep:
+                keep[k] = buf
+
+    # closed loop: at most `window` requests in flight
+    srv = ccl.ccl_server_create(local, n_streams=args.streams, max_batch=1024, host_staging_bytes=4 << 30)
+    warm = [submit(srv, lat) for lat in pool[:16]]
+    drain(srv, warm, pool[:16])
+    clocks = ClockSampler(local)
+    clocks.start()
+    done_at = [0.0] * len(req)
+    tickets = [None] * len(req)
+    sem = threading.Semaphore(args.window)
+
+    def feeder():
+        for k, lat in enumerate(req):
+            sem.acquire()
+            tickets[k] = submit(srv, lat)
+
+    keep = {k: None for k in range(0, len(req), max(1, len(req) // args.parity_sample))}
+    t0 = time.perf_counter()
+    th = threading.Thread(target=feeder)
+    th.start()
+    for k, lat in enumerate(req):
+        while tickets[k] is None:
+            time.sleep(0.00005)
+        buf = np.empty(lat.n, np.int32) if k in keep else out_bufs[id(lat)]
+        ccl.check(ccl.ccl_server_wait(srv, tickets[k], buf, 600_000), "ccl_server_wait")
+        if k in keep:
+            keep[k] = buf
+        done_at[k] = time.perf_counter()
+        sem.release()
+    th.join()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    st_closed = ccl.ccl_server_stats_get(srv)
+    ccl.ccl_server_destroy(srv)
+    total_sites = sum(lat.n for lat in req)
+    capacity = total_sites / wall
+
+    # open loop: Poisson arrivals at load x capacity
+    loads = {}
+    for load in args.loads:
+        rate = load * capacity / mean_sites            # requests per second
+        rng = np.random.default_rng(55 + rank)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(req)))
+        srv = ccl.ccl_server_create(local, n_streams=args.streams, max_batch=1024, host_staging_bytes=4 << 30)
+        drain(srv, [submit(srv, lat) for lat in pool[:16]], pool[:16])
+        tk = [None] * len(req)
+
+        def open_feeder():
+            base = time.perf_counter()
+            for k, lat in enumerate(req):
+                delay = base + arrivals[k] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                tk[k] = submit(srv, lat)
+
+        t1 = time.perf_counter()
+        th = threading.Thread(target=open_feeder)
+        th.start()
+        for k, lat in enumerate(req):
+            while tk[k] is None:
+                time.sleep(0.00005)
+            ccl.check(ccl.ccl_server_wait(srv, tk[k], out_bufs[id(lat)], 600_000), "ccl_server_wait")
+        th.join()
+        el = time.perf_counter() - t1
+        so = ccl.ccl_server_stats_get(srv)
+        ccl.ccl_server_destroy(srv)
+        # the server's percentiles cover the 16 warm-up requests too (tiny next to the stream)
+        loads[str(load)] = {"offered_req_per_s": rate, "achieved_sites_per_s": total_sites / el,
+                            "p50_ms": so.p50_ms, "p99_ms": so.p99_ms, "max_ms": so.max_ms,
+                            "batches": int(so.batches)}
+
+    ok = all(np.array_equal(buf, oracle.uf_label(req[k])) for k, buf in keep.items())
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            t2, sites, done = time.perf_counter(), 0, 0
+            for lat in pool:
+                oracle.uf_label(lat)
+                sites += lat.n
+                done += 1
+                if time.perf_counter() - t2 > args.cpu_seconds:
+                    break
+            cpu = {"value": sites / (time.perf_counter() - t2), "unit": "sites/s", "cores": 1,
+                   "kind": "oracle", "sample": f"union-find oracle over {done} pool requests ({sites} sites), 1 thread"}
+        h2d = sum(4 * (lat.n + 1) + 4 * lat.nnz + 4 * lat.open_bits.size for lat in req) / len(req)
+        line = {
+            "metric": "sites labeled/s (served)", "value": world * capacity, "unit": "sites/s",
+            "n_gpus": world, "steps": len(req), "warmup": 16, "ms_per_step": 1e3 * wall / len(req),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": "served", "requests": len(req), "pool": len(pool),
+                       "mean_sites": mean_sites, "window": args.window, "streams": args.streams,
+                       "generation_s": t_gen, "l2": "inputs larger than L2 in aggregate (no flush)"},
+            "closed_loop": {"wall_s": wall, "requests_per_s": len(req) / wall, "batches": int(st_closed.batches),
+                            "p50_ms": st_closed.p50_ms, "p99_ms": st_closed.p99_ms},
+            "open_loop": loads,
+            "e2e": {"value": world * capacity, "unit": "sites/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": 4 * mean_sites,
+                    "entry": "ccl_server_submit / ccl_server_wait (host arrays in, labels out)"},
+            "roofline": None,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "parity_sample": {"requests": len(keep), "ok": ok},
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=sorted(CONFIGS) + ["batched"], default="tri4096")
+    ap.add_argument("--config", choices=sorted(CONFIGS) + ["batched", "served"], default="tri4096")
     ap.add_argument("--instances", type=int, default=4096)
     ap.add_argument("--parity-sample", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--requests", type=int, default=2000, help="served: requests in the stream")
+    ap.add_argument("--pool", type=int, default=128, help="served: distinct pre-generated requests")
+    ap.add_argument("--window", type=int, default=64, help="served: requests in flight (closed loop)")
+    ap.add_argument("--streams", type=int, default=2, help="served: server compute streams")
+    ap.add_argument("--loads", type=float, nargs="*", default=[0.5, 0.8],
+                    help="served: open-loop arrival rates as fractions of the capacity")
     ap.add_argument("--input", choices=["csr", "dense", "random", "dense-random"], default="csr",
                     help="single-instance configs: CSR with bit words (default), the dense strided "
                          "neighbour list, or either with bonds drawn on the device")
@@ -599,6 +772,8 @@ def main():
         run_reference(args, rank, world)
     elif args.config == "batched":
         run_batched(args, rank, world, local)
+    elif args.config == "served":
+        run_served(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
 

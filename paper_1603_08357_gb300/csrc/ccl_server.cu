@@ -86,6 +86,74 @@ const uint32_t *h_bits(const Req &r) {
 }
 int32_t *h_labels(Req &r) { return r.h ? (int32_t *)(r.h + HostLayout(r.n, r.nnz).lab) : r.v_labels.data(); }
 
+// Host copies between caller memory and the pinned staging arena, split
+// across a few persistent threads: one thread moves about 10 GB/s, well
+// below what the host memory and the host-device link sustain, and a
+// request of 10^6 sites carries about 16 MB.
+class CopyPool {
+  public:
+    explicit CopyPool(int n_threads) {
+        for (int t = 0; t < n_threads; ++t) workers_.emplace_back([this] { run(); });
+    }
+    ~CopyPool() {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto &w : workers_) w.join();
+    }
+    // Copies `bytes` from src to dst; returns when the copy is complete.
+    void copy(void *dst, const void *src, size_t bytes) {
+        const size_t parts = std::min<size_t>(workers_.size() + 1, bytes / kMinPiece);
+        if (parts <= 1) { memcpy(dst, src, bytes); return; }
+        const size_t piece = ((bytes + parts - 1) / parts + 63) & ~size_t(63);
+        std::atomic<size_t> left{0};
+        size_t queued = 0;
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            for (size_t off = piece; off < bytes; off += piece) {
+                q_.push_back(Piece{(char *)dst + off, (const char *)src + off, std::min(piece, bytes - off), &left});
+                ++queued;
+            }
+            left.store(queued);
+        }
+        cv_.notify_all();
+        memcpy(dst, src, std::min(piece, bytes));     // the caller copies the first piece
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_done_.wait(lk, [&] { return left.load() == 0; });
+    }
+
+  private:
+    struct Piece {
+        char *dst;
+        const char *src;
+        size_t bytes;
+        std::atomic<size_t> *left;
+    };
+    static constexpr size_t kMinPiece = 1 << 20;
+    void run() {
+        for (;;) {
+            Piece pc;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [&] { return stop_ || !q_.empty(); });
+                if (stop_ && q_.empty()) return;
+                pc = q_.front();
+                q_.pop_front();
+            }
+            memcpy(pc.dst, pc.src, pc.bytes);
+            std::lock_guard<std::mutex> lk(mu_);
+            if (pc.left->fetch_sub(1) == 1) cv_done_.notify_all();
+        }
+    }
+    std::mutex mu_;
+    std::condition_variable cv_, cv_done_;
+    std::deque<Piece> q_;
+    std::vector<std::thread> workers_;
+    bool stop_ = false;
+};
+
 // First-fit allocator over one pinned host buffer (callers hold the server mutex).
 struct HostArena {
     char *base = nullptr;
@@ -130,6 +198,7 @@ struct ccl_server {
     cudaMemPool_t pool = nullptr;
     char *h_stage = nullptr;
     HostArena arena;
+    std::unique_ptr<CopyPool> copier;
 
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -405,6 +474,10 @@ ccl_status ccl_server_create(ccl_server **out, const ccl_server_config *cfg_in) 
         return CCL_ERR_CUDA;
     }
     S->slot_busy.assign(S->streams.size(), false);
+    {
+        const unsigned hw = std::max(2u, std::thread::hardware_concurrency());
+        S->copier.reset(new CopyPool((int)std::min(8u, hw / 2)));
+    }
     S->th = std::thread(server_loop, S);
     *out = S;
     return CCL_OK;
@@ -436,10 +509,10 @@ ccl_status ccl_server_submit(ccl_server *S, const ccl_request *req, uint64_t *ti
         if (r->h) r->h_bytes = lay.total;
     }
     if (r->h) {
-        memcpy(r->h, req->row_ptr, (size_t)(r->n + 1) * 4);
+        S->copier->copy(r->h, req->row_ptr, (size_t)(r->n + 1) * 4);
         if (r->nnz > 0) {
-            memcpy(r->h + lay.ci, req->col_idx, (size_t)r->nnz * 4);
-            memcpy(r->h + lay.bits, req->open_bits, (size_t)((r->nnz + 31) / 32) * 4);
+            S->copier->copy(r->h + lay.ci, req->col_idx, (size_t)r->nnz * 4);
+            S->copier->copy(r->h + lay.bits, req->open_bits, (size_t)((r->nnz + 31) / 32) * 4);
         }
     } else {
         r->v_row_ptr.assign(req->row_ptr, req->row_ptr + r->n + 1);
@@ -469,11 +542,18 @@ ccl_status ccl_server_wait(ccl_server *S, uint64_t ticket, int32_t *labels_host,
     auto ready = [&] { return r->done; };
     if (timeout_ms < 0) S->cv_done.wait(lk, ready);
     else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) return CCL_ERR_TIMEOUT;
-    if (labels_host && r->n > 0) memcpy(labels_host, h_labels(*r), (size_t)r->n * 4);
+    if (labels_host && r->n > 0) {
+        // copy outside the lock: the request is done and only this waiter owns it now
+        S->tickets.erase(ticket);
+        lk.unlock();
+        S->copier->copy(labels_host, h_labels(*r), (size_t)r->n * 4);
+        lk.lock();
+    } else {
+        S->tickets.erase(ticket);
+    }
     if (r->h) { S->arena.release(r->h, r->h_bytes); r->h = nullptr; }
     r->v_labels.clear();
     r->v_labels.shrink_to_fit();
-    S->tickets.erase(ticket);
     return r->status;
 }
 
@@ -509,6 +589,7 @@ void ccl_server_destroy(ccl_server *S) {
     }
     S->cv_work.notify_all();
     if (S->th.joinable()) S->th.join();
+    S->copier.reset();
     cudaSetDevice(S->cfg.device);
     for (auto c : S->ctxs) ccl_context_destroy(c);
     for (auto s : S->streams) cudaStreamDestroy(s);
