@@ -149,8 +149,16 @@ def replica_spec(name: str, rank: int) -> dict:
     return c
 
 
+P_OVERRIDE = None      # --p: the bond probability of a single-instance config
+
+
 def make_workload(name: str, rank: int):
-    return L.make_instance(replica_spec(name, rank)), CONFIGS[name]["desc"]
+    spec = replica_spec(name, rank)
+    desc = CONFIGS[name]["desc"]
+    if P_OVERRIDE is not None:
+        spec["p"] = P_OVERRIDE
+        desc = desc.replace(f"p={CONFIGS[name]['p']}", f"p={P_OVERRIDE}")
+    return L.make_instance(spec), desc
 
 
 def max_over_ranks(value: float, dist, device=None) -> float:
@@ -448,7 +456,7 @@ def run_ours(args, rank, world, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
-            "config": {"workload": workload, "desc": desc, "input": kind, "width": width or None,
+            "config": {"workload": workload, "desc": desc, "p": lat.p, "input": kind, "width": width or None,
                        "n_sites": lat.n, "nnz": lat.nnz,
                        "residual_pairs": q, "options": opts, "autotune": tuned,
                        "l2": "inputs larger than L2 (no flush)" if lat.nnz * 4 > L2_BYTES
@@ -766,7 +774,11 @@ def main():
     ap.add_argument("--input", choices=["csr", "dense", "random", "dense-random"], default="csr",
                     help="single-instance configs: CSR with bit words (default), the dense strided "
                          "neighbour list, or either with bonds drawn on the device")
+    ap.add_argument("--p", type=float, default=None,
+                    help="single-instance configs: bond probability in place of the config's")
     args = ap.parse_args()
+    global P_OVERRIDE
+    P_OVERRIDE = args.p
     rank, world, local = _env_rank()
     if args.impl == "reference":
         run_reference(args, rank, world)
