@@ -546,7 +546,12 @@ __global__ void __launch_bounds__(256) k_reduce(Params P) {
 #endif
     for (long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nwin; w += nwarps) {
         const long long wbeg = w * win;
-        const long long wend = min(wbeg + win, total);
+        const int wlen = (int)(min(wbeg + win, total) - wbeg);
+        // A pair needs at most 4n + 8 rounds (its chains and Algorithm 1's loop
+        // are bounded by the instance's n <= 32 n_chunks); a lane serves at most
+        // wlen pairs. Past this many rounds the window is abandoned with an error.
+        const long long round_cap = (128ll * P.n_chunks + 8) * (long long)wlen;
+        long long rounds = 0;
         // band of the window's first pair (all lanes search; smem broadcast)
         int band = 0;
         {
@@ -557,39 +562,40 @@ __global__ void __launch_bounds__(256) k_reduce(Params P) {
             }
             band = lo;
         }
-        long long next = wbeg;
+        int nxt = 0;        // pairs of the window handed to slots so far
         int32_t *L[kRedSlots];
-        int32_t cap[kRedSlots], a[kRedSlots], b[kRedSlots], it[kRedSlots], st[kRedSlots];
+        int32_t a[kRedSlots], b[kRedSlots], st[kRedSlots];
 #pragma unroll
         for (int u = 0; u < kRedSlots; ++u) {
             st[u] = kTaskDone;
             L[u] = P.one.labels;
-            cap[u] = P.one.n;
-            a[u] = b[u] = it[u] = 0;
+            a[u] = b[u] = 0;
         }
         for (;;) {
-            // refill empty slots with the window's next pairs, in order
+            // refill empty slots with the window's next pairs, in order (the
+            // tests are warp-uniform: nothing runs once the window is handed out)
+            if (nxt < wlen) {
 #pragma unroll
-            for (int u = 0; u < kRedSlots; ++u) {
-                const unsigned need = __ballot_sync(kFull, st[u] == kTaskDone);
-                const long long p = next + __popc(need & lt);
-                if (st[u] == kTaskDone && p < wend) {
-                    int bb = band;
-                    while (s_pref[bb + 1] <= p) ++bb;
-                    const long long slot = P.band[bb].qbase + (p - s_pref[bb]);
-                    const int2 pr = P.q[slot];
-                    if (kBatched) {
-                        const int k = P.qk[slot];
-                        L[u] = P.insts[k].labels;
-                        cap[u] = P.insts[k].n;
+                for (int u = 0; u < kRedSlots; ++u) {
+                    const unsigned need = __ballot_sync(kFull, st[u] == kTaskDone);
+                    if (need == 0) continue;
+                    const int pos = nxt + __popc(need & lt);
+                    if (st[u] == kTaskDone && pos < wlen) {
+                        const long long p = wbeg + pos;
+                        int bb = band;
+                        while (s_pref[bb + 1] <= p) ++bb;
+                        const long long slot = P.band[bb].qbase + (p - s_pref[bb]);
+                        const int2 pr = P.q[slot];
+                        if (kBatched) L[u] = P.insts[P.qk[slot]].labels;
+                        a[u] = max(pr.x, pr.y);
+                        b[u] = min(pr.x, pr.y);
+                        st[u] = kTaskChase;
                     }
-                    a[u] = max(pr.x, pr.y);
-                    b[u] = min(pr.x, pr.y);
-                    st[u] = kTaskChase;
-                    it[u] = 0;
+                    nxt = min(nxt + __popc(need), wlen);
+                    const long long pn = wbeg + nxt;
+                    while (band < P.n_bands - 1 && s_pref[band + 1] <= pn) ++band;
+                    if (nxt >= wlen) break;
                 }
-                next = min(next + (long long)__popc(need), wend);
-                while (band < P.n_bands - 1 && s_pref[band + 1] <= next) ++band;
             }
 #ifdef CCL_DEVICE_STATS
             st_iter++;
@@ -631,13 +637,13 @@ __global__ void __launch_bounds__(256) k_reduce(Params P) {
                     else if (old > b[u]) a[u] = old;
                     else { a[u] = b[u]; b[u] = old; }
                 }
-                if (st[u] != kTaskDone && ++it[u] > 4 * cap[u] + 8) {
-                    raise_err(P.err, kErrNonconv);
-                    st[u] = kTaskDone;
-                }
                 any |= st[u] != kTaskDone;
             }
-            if (!__any_sync(kFull, any) && next >= wend) break;
+            if (!__any_sync(kFull, any) && nxt >= wlen) break;
+            if (++rounds > round_cap) {
+                raise_err(P.err, kErrNonconv);
+                break;
+            }
         }
     }
 #ifdef CCL_DEVICE_STATS
