@@ -308,7 +308,8 @@ def run_ours(args, rank, world, local):
         tuned = {"best_ms": best_ms}
     opts = {name: ccl.ccl_get_option(ctx, o) for name, o in (
         ("threads", ccl.CCL_OPT_BLOCK_THREADS), ("ctas_per_sm", ccl.CCL_OPT_CTAS_PER_SM),
-        ("pre_analysis", ccl.CCL_OPT_PRE_ANALYSIS), ("link_mode", ccl.CCL_OPT_LINK_MODE))}
+        ("pre_analysis", ccl.CCL_OPT_PRE_ANALYSIS), ("link_mode", ccl.CCL_OPT_LINK_MODE),
+        ("refill", ccl.CCL_OPT_REFILL))}
 
     def step():
         if kind == "csr":

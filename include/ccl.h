@@ -86,9 +86,13 @@ typedef enum {
     CCL_OPT_PROFILE = 3,       /* 1: record CUDA events between the steps (ccl_get_step_times);
                                   setting it restarts the averaging */
     CCL_OPT_CTAS_PER_SM = 4,   /* persistent CTAs per SM of the analysis kernel; 0 (default) = occupancy maximum */
-    CCL_OPT_LINK_MODE = 5      /* step (iii): 0 (default) a root is linked under the other tree's
+    CCL_OPT_LINK_MODE = 5,     /* step (iii): 0 (default) a root is linked under the other tree's
                                   root, as in Algorithm 1; 1 under the node the other chain has
                                   reached (same atomicMin loop, shorter walks on trees) */
+    CCL_OPT_REFILL = 6         /* step (iii): 1 (default) each thread serves a fixed stride of the
+                                  residual pairs and loads its next one ahead; 0 a warp hands its
+                                  pairs out in order to whichever threads are free (balances
+                                  uneven chains) */
 } ccl_option;
 
 CCL_API ccl_status ccl_set_option(ccl_context *ctx, int option, int64_t value);
@@ -282,7 +286,8 @@ CCL_API ccl_status ccl_get_step_times(ccl_context *ctx, float *ms, int32_t n);
 
 /*
  * ccl_autotune -- synchronous: times the labelling of the given instance under
- * candidate settings (analysis threads per CTA, step (ii) on/off, link mode)
+ * candidate settings (analysis threads per CTA, step (ii) on/off, link mode,
+ * refill mode)
  * and keeps the fastest for instances of this size class (log2 of the site
  * count, mean degree rounded); the choice also becomes the context's
  * options (ccl_get_option reports it). Every candidate writes the same labels,

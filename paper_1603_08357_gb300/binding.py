@@ -35,6 +35,7 @@ CCL_OPT_USE_GRAPHS = 2
 CCL_OPT_PROFILE = 3
 CCL_OPT_CTAS_PER_SM = 4
 CCL_OPT_LINK_MODE = 5
+CCL_OPT_REFILL = 6
 
 
 class CclError(RuntimeError):

@@ -29,6 +29,7 @@ struct TuneChoice {
     int ctas_per_sm = 0;
     int pre_analysis = 1;
     int link_mode = 0;
+    int refill = 1;         // step (iii): 1 static per-lane pairs, 0 in-order hand-out
 };
 
 struct GraphEntry {
@@ -140,8 +141,8 @@ int blocks_per_sm(ccl_context *ctx, int kernel_id, int threads) {
         case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init<true>, kInitThreads, kInitSmem); break;
         case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_analysis<false>, threads, 0); break;
         case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_analysis<true>, threads, 0); break;
-        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_reduce<false>, threads, 0); break;
-        case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_reduce<true>, threads, 0); break;
+        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_reduce<false, true>, threads, 0); break;
+        case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_reduce<true, true>, threads, 0); break;
         case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init<false, true>, kInitThreads, kInitSmem); break;
         case 7: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init_dense<false>, kDenseThreads, 0); break;
         case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init_dense<true>, kDenseThreads, 0); break;
@@ -249,8 +250,13 @@ ccl_status enqueue_steps(ccl_context *ctx, const Params &P0, bool batched, const
         CCL_CUDA(cudaGetLastError());
     }
     if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[2], s));
-    if (batched) k_reduce<true><<<(unsigned)g_red, 256, 0, s>>>(P);
-    else k_reduce<false><<<(unsigned)g_red, 256, 0, s>>>(P);
+    if (batched) {
+        if (tc.refill) k_reduce<true, true><<<(unsigned)g_red, 256, 0, s>>>(P);
+        else k_reduce<true, false><<<(unsigned)g_red, 256, 0, s>>>(P);
+    } else {
+        if (tc.refill) k_reduce<false, true><<<(unsigned)g_red, 256, 0, s>>>(P);
+        else k_reduce<false, false><<<(unsigned)g_red, 256, 0, s>>>(P);
+    }
     CCL_CUDA(cudaGetLastError());
     if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[3], s));
     if (batched) k_analysis<true><<<(unsigned)grid_for(ctx, 3, tc, warps_chunks), T, 0, s>>>(P);
@@ -268,7 +274,7 @@ uint64_t fnv1a(const void *data, size_t bytes, uint64_t h = 1469598103934665603u
 
 bool same_choice(const TuneChoice &a, const TuneChoice &b) {
     return a.threads == b.threads && a.ctas_per_sm == b.ctas_per_sm &&
-           a.pre_analysis == b.pre_analysis && a.link_mode == b.link_mode;
+           a.pre_analysis == b.pre_analysis && a.link_mode == b.link_mode && a.refill == b.refill;
 }
 
 GraphEntry *find_graph(ccl_context *ctx, const GraphEntry &key) {
@@ -594,10 +600,10 @@ ccl_status ccl_context_create(ccl_context **out, int device) {
     if (const char *env = getenv("CCL_TUNE_CACHE")) {
         if (FILE *f = fopen(env, "r")) {
             long long cls;
-            int a, b, c, d;
-            while (fscanf(f, "%lld %d %d %d %d", &cls, &a, &b, &c, &d) == 5) {
+            int a, b, c, d, r;
+            while (fscanf(f, "%lld %d %d %d %d %d", &cls, &a, &b, &c, &d, &r) == 6) {
                 TuneChoice t;
-                t.threads = a; t.ctas_per_sm = b; t.pre_analysis = c; t.link_mode = d;
+                t.threads = a; t.ctas_per_sm = b; t.pre_analysis = c; t.link_mode = d; t.refill = r ? 1 : 0;
                 if (t.threads >= 64 && t.threads <= 512 && t.threads % 32 == 0) ctx->tune_table[cls] = t;
             }
             fclose(f);
@@ -650,6 +656,7 @@ ccl_status ccl_set_option(ccl_context *ctx, int option, int64_t value) {
             ctx->opt.ctas_per_sm = (int)value;
             break;
         case CCL_OPT_LINK_MODE: ctx->opt.link_mode = value ? 1 : 0; break;
+        case CCL_OPT_REFILL: ctx->opt.refill = value ? 1 : 0; break;
         default: return CCL_ERR_INVALID_ARGUMENT;
     }
     // explicit options take effect over any tuned entry
@@ -666,6 +673,7 @@ ccl_status ccl_get_option(ccl_context *ctx, int option, int64_t *value) {
         case CCL_OPT_PROFILE: *value = ctx->profile; break;
         case CCL_OPT_CTAS_PER_SM: *value = ctx->opt.ctas_per_sm; break;
         case CCL_OPT_LINK_MODE: *value = ctx->opt.link_mode; break;
+        case CCL_OPT_REFILL: *value = ctx->opt.refill; break;
         default: return CCL_ERR_INVALID_ARGUMENT;
     }
     return CCL_OK;
@@ -986,11 +994,12 @@ ccl_status ccl_autotune(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t 
     std::vector<TuneChoice> cands;
     for (int T : {128, 256, 512})
         for (int pre = 0; pre < 2; ++pre)
-            for (int lm = 0; lm < 2; ++lm) {
-                TuneChoice tc;
-                tc.threads = T; tc.ctas_per_sm = 0; tc.pre_analysis = pre; tc.link_mode = lm;
-                cands.push_back(tc);
-            }
+            for (int lm = 0; lm < 2; ++lm)
+                for (int rf = 0; rf < 2; ++rf) {
+                    TuneChoice tc;
+                    tc.threads = T; tc.ctas_per_sm = 0; tc.pre_analysis = pre; tc.link_mode = lm; tc.refill = rf;
+                    cands.push_back(tc);
+                }
     for (const TuneChoice &tc : cands) {
         float tmin = 1e30f;
         for (int rep = 0; rep < 4 && st == CCL_OK; ++rep) {
@@ -1015,8 +1024,8 @@ ccl_status ccl_autotune(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t 
     if (const char *env = getenv("CCL_TUNE_CACHE")) {
         if (FILE *f = fopen(env, "w")) {
             for (auto &kv : ctx->tune_table)
-                fprintf(f, "%lld %d %d %d %d\n", (long long)kv.first, kv.second.threads,
-                        kv.second.ctas_per_sm, kv.second.pre_analysis, kv.second.link_mode);
+                fprintf(f, "%lld %d %d %d %d %d\n", (long long)kv.first, kv.second.threads,
+                        kv.second.ctas_per_sm, kv.second.pre_analysis, kv.second.link_mode, kv.second.refill);
             fclose(f);
         }
     }

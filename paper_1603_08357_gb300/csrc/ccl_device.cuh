@@ -509,7 +509,14 @@ enum : int32_t { kTaskDone = 0, kTaskChase = 1, kTaskRoot = 2, kTaskMerge = 3 };
 // through an atomicMin whose returned value is current.
 __device__ __forceinline__ int32_t red_load(const int32_t *p) { return __ldca(p); }
 
-template <bool kBatched>
+// Two ways of handing a window's pairs to the slots:
+//  kStatic = false: every round, the warp's empty slots take the window's
+//    next pairs in order (ballot + popc), which balances lanes whose chains
+//    differ in length (randomly numbered trees);
+//  kStatic = true: lane l serves pairs wbeg + l, wbeg + l + 32, ... and loads
+//    its next pair a round before a slot needs it: fewer instructions per
+//    round and no exposed queue load (lattices).
+template <bool kBatched, bool kStatic>
 __global__ void __launch_bounds__(256) k_reduce(Params P) {
     __shared__ long long s_pref[kMaxBands + 1];
     if (threadIdx.x < 32) {
@@ -563,6 +570,21 @@ __global__ void __launch_bounds__(256) k_reduce(Params P) {
             band = lo;
         }
         int nxt = 0;        // pairs of the window handed to slots so far
+        // kStatic: the lane's next pair, loaded ahead
+        long long pnext = wbeg + lane;
+        const long long wend = wbeg + wlen;
+        int cur = band;             // band cursor of this lane (its pairs increase)
+        int2 pf = make_int2(0, 0);
+        int pfk = 0;
+        bool pf_ok = false;
+        auto fetch = [&](long long p) {
+            while (s_pref[cur + 1] <= p) ++cur;
+            const long long slot = P.band[cur].qbase + (p - s_pref[cur]);
+            pf = P.q[slot];
+            if (kBatched) pfk = P.qk[slot];
+            pf_ok = true;
+        };
+        if (kStatic && pnext < wend) { fetch(pnext); pnext += 32; }
         int32_t *L[kRedSlots];
         int32_t a[kRedSlots], b[kRedSlots], st[kRedSlots];
 #pragma unroll
@@ -572,29 +594,46 @@ __global__ void __launch_bounds__(256) k_reduce(Params P) {
             a[u] = b[u] = 0;
         }
         for (;;) {
-            // refill empty slots with the window's next pairs, in order (the
-            // tests are warp-uniform: nothing runs once the window is handed out)
-            if (nxt < wlen) {
+            if (kStatic) {
+                // at most one empty slot per lane and round takes the prefetched pair
+                int take = -1;
 #pragma unroll
-                for (int u = 0; u < kRedSlots; ++u) {
-                    const unsigned need = __ballot_sync(kFull, st[u] == kTaskDone);
-                    if (need == 0) continue;
-                    const int pos = nxt + __popc(need & lt);
-                    if (st[u] == kTaskDone && pos < wlen) {
-                        const long long p = wbeg + pos;
-                        int bb = band;
-                        while (s_pref[bb + 1] <= p) ++bb;
-                        const long long slot = P.band[bb].qbase + (p - s_pref[bb]);
-                        const int2 pr = P.q[slot];
-                        if (kBatched) L[u] = P.insts[P.qk[slot]].labels;
-                        a[u] = max(pr.x, pr.y);
-                        b[u] = min(pr.x, pr.y);
-                        st[u] = kTaskChase;
+                for (int u = kRedSlots - 1; u >= 0; --u)
+                    if (st[u] == kTaskDone) take = u;
+                if (take >= 0 && pf_ok) {
+                    const int32_t na = max(pf.x, pf.y), nb = min(pf.x, pf.y);
+                    int32_t *nl = kBatched ? P.insts[pfk].labels : P.one.labels;
+#pragma unroll
+                    for (int u = 0; u < kRedSlots; ++u)
+                        if (u == take) { a[u] = na; b[u] = nb; st[u] = kTaskChase; L[u] = nl; }
+                    pf_ok = false;
+                    if (pnext < wend) { fetch(pnext); pnext += 32; }
+                }
+            } else {
+                // refill empty slots with the window's next pairs, in order (the
+                // tests are warp-uniform: nothing runs once the window is handed out)
+                if (nxt < wlen) {
+#pragma unroll
+                    for (int u = 0; u < kRedSlots; ++u) {
+                        const unsigned need = __ballot_sync(kFull, st[u] == kTaskDone);
+                        if (need == 0) continue;
+                        const int pos = nxt + __popc(need & lt);
+                        if (st[u] == kTaskDone && pos < wlen) {
+                            const long long p = wbeg + pos;
+                            int bb = band;
+                            while (s_pref[bb + 1] <= p) ++bb;
+                            const long long slot = P.band[bb].qbase + (p - s_pref[bb]);
+                            const int2 pr = P.q[slot];
+                            if (kBatched) L[u] = P.insts[P.qk[slot]].labels;
+                            a[u] = max(pr.x, pr.y);
+                            b[u] = min(pr.x, pr.y);
+                            st[u] = kTaskChase;
+                        }
+                        nxt = min(nxt + __popc(need), wlen);
+                        const long long pn = wbeg + nxt;
+                        while (band < P.n_bands - 1 && s_pref[band + 1] <= pn) ++band;
+                        if (nxt >= wlen) break;
                     }
-                    nxt = min(nxt + __popc(need), wlen);
-                    const long long pn = wbeg + nxt;
-                    while (band < P.n_bands - 1 && s_pref[band + 1] <= pn) ++band;
-                    if (nxt >= wlen) break;
                 }
             }
 #ifdef CCL_DEVICE_STATS
@@ -639,7 +678,7 @@ __global__ void __launch_bounds__(256) k_reduce(Params P) {
                 }
                 any |= st[u] != kTaskDone;
             }
-            if (!__any_sync(kFull, any) && nxt >= wlen) break;
+            if (!__any_sync(kFull, any || pf_ok) && (kStatic || nxt >= wlen)) break;
             if (++rounds > round_cap) {
                 raise_err(P.err, kErrNonconv);
                 break;

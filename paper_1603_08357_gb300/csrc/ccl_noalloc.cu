@@ -72,7 +72,7 @@ ccl_status setup_device(int dev, DeviceSetup **out) {
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.ana_per_sm, k_analysis<false>, 256, 0);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.red_per_sm, k_reduce<false>, 256, 0);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.red_per_sm, k_reduce<false, true>, 256, 0);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
             return e == cudaErrorMemoryAllocation ? CCL_ERR_OUT_OF_MEMORY : CCL_ERR_CUDA;
@@ -149,7 +149,7 @@ extern "C" ccl_status ccl_label_noalloc(int32_t n, int64_t nnz, const int32_t *r
     if (e == cudaSuccess) {
         k_init<false><<<(unsigned)g_init, kInitThreads, kInitSmem, s>>>(P);
         k_analysis<false><<<(unsigned)g_ana, 256, 0, s>>>(P);
-        k_reduce<false><<<(unsigned)g_red, 256, 0, s>>>(P);
+        k_reduce<false, true><<<(unsigned)g_red, 256, 0, s>>>(P);
         k_analysis<false><<<(unsigned)g_ana, 256, 0, s>>>(P);
         e = cudaGetLastError();
     }

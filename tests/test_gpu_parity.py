@@ -96,11 +96,13 @@ def test_standard_bethe_has_no_residual_pairs(ctx, z, S):
 @pytest.mark.parametrize("threads", [64, 128, 256, 512])
 @pytest.mark.parametrize("pre", [0, 1])
 @pytest.mark.parametrize("link", [0, 1])
-def test_launch_options_same_labels(threads, pre, link):
+@pytest.mark.parametrize("refill", [0, 1])
+def test_launch_options_same_labels(threads, pre, link, refill):
     c = ccl.ccl_context_create(0)
     try:
         for opt, val in ((ccl.CCL_OPT_BLOCK_THREADS, threads), (ccl.CCL_OPT_PRE_ANALYSIS, pre),
-                         (ccl.CCL_OPT_LINK_MODE, link), (ccl.CCL_OPT_CTAS_PER_SM, 1 if threads == 64 else 0)):
+                         (ccl.CCL_OPT_LINK_MODE, link), (ccl.CCL_OPT_REFILL, refill),
+                         (ccl.CCL_OPT_CTAS_PER_SM, 1 if threads == 64 else 0)):
             assert ccl.ccl_set_option(c, opt, val) == ccl.CCL_OK
         lat = L.triangle(300, 0.52, 11)
         want = oracle.uf_label(lat)
@@ -261,3 +263,27 @@ def test_graph_replay_keyed_on_sizes(ctx):
         assert ccl.ccl_label(ctx, lat.n, lat.nnz, rp, ci, bits, out) == ccl.CCL_OK
         assert ccl.ccl_sync(ctx) == ccl.CCL_OK
         assert np.array_equal(out[:lat.n].cpu().numpy(), oracle.uf_label(lat))
+
+
+@pytest.mark.parametrize("refill", [0, 1])
+def test_refill_modes_on_uneven_work(refill):
+    """Both ways of handing residual pairs to threads, on inputs whose chains
+    differ widely in length: a randomly numbered tree, a multigraph, and a
+    batch of mixed instances."""
+    from ccl_testutil import gpu_label_batched
+    c = ccl.ccl_context_create(0)
+    try:
+        assert ccl.ccl_set_option(c, ccl.CCL_OPT_REFILL, refill) == ccl.CCL_OK
+        assert ccl.ccl_set_option(c, ccl.CCL_OPT_PRE_ANALYSIS, 0) == ccl.CCL_OK
+        for lat in (L.cayley(3, 17, 0.5, 3, perm_seed=5), L.random_graph(50000, 90000, 4),
+                    L.triangle(1000, 0.6, 3)):
+            assert np.array_equal(gpu_label(c, lat), oracle.uf_label(lat))
+        b = L.make_batch(L.batched_mix_specs(48, seed=21))
+        got = gpu_label_batched(c, b)
+        for k in range(b.k):
+            s0, s1 = int(b.site_off[k]), int(b.site_off[k + 1])
+            assert np.array_equal(got[s0:s1], oracle.uf_label(b.instance(k)))
+        v = ccl.ccl_get_option(c, ccl.CCL_OPT_REFILL)
+        assert v == refill
+    finally:
+        ccl.ccl_context_destroy(c)
