@@ -254,11 +254,17 @@ struct TileCtx {
 // stage barriers): a site whose smallest open lower neighbour m lies in such
 // a tile takes label[m] (the root of m's tree after steps (i)/(ii)) instead of
 // m, which shortcuts the chain step (ii) would walk.
+// What the emission of a scanned chunk needs (per lane).
+struct ChunkRes {
+    int32_t i, a, a_next, mk;
+    uint32_t resmask;
+    int32_t r;          // residual pairs of the lane's site
+    bool fast;          // warp-uniform: the register path scanned the chunk
+};
+
 template <bool kBatched, bool kGen = false>
-__device__ __forceinline__ void init_consume_chunk(const Params &P, const Stage &S, const Inst &I,
-                                                   int cc, int lane, const TileCtx &tc,
-                                                   unsigned long long *band_cnt,
-                                                   unsigned long long &my_pairs) {
+__device__ __forceinline__ void init_scan_chunk(const Params &P, const Stage &S, const Inst &I,
+                                                int cc, int lane, const TileCtx &tc, ChunkRes &cr) {
     const StageHdr &h = S.h;
     const int32_t n = I.n;
     const int32_t s0 = h.s0 + cc * kChunk;
@@ -326,34 +332,39 @@ __device__ __forceinline__ void init_consume_chunk(const Params &P, const Stage 
     }
     if (i < n) I.labels[i] = lab;
 
-    const int r = cnt > 1 ? cnt - 1 : 0;
-    const int incl = warp_incl_scan(r, lane);
-    const int total = __shfl_sync(kFull, incl, 31);
-    if (total == 0) return;
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(band_cnt, (unsigned long long)total);
-    base = __shfl_sync(kFull, base, 0);
-    if (lane == 0) my_pairs += (unsigned long long)total;
-    if (r > 0) {
-        int64_t slot = h.qband + (int64_t)base + (incl - r);
-        if (slot + r > P.q_cap) { raise_err(P.err, kErrIndex); return; }   // corrupt rows only
-        if (all_fast) {
-            const int32_t *col = S.ci + (a - h.ci_lo);
-            while (resmask) {
-                const int t = __ffs(resmask) - 1;
-                resmask &= resmask - 1;
-                P.q[slot] = make_int2(i, col[t]);
+    cr.i = i;
+    cr.a = a;
+    cr.a_next = a_next;
+    cr.mk = mk;
+    cr.resmask = resmask;
+    cr.fast = all_fast;
+    cr.r = cnt > 1 ? cnt - 1 : 0;
+}
+
+// Writes the residual pairs of one scanned chunk from queue slot `slot` on.
+template <bool kBatched, bool kGen = false>
+__device__ __forceinline__ void init_emit_chunk(const Params &P, const Stage &S, const Inst &I,
+                                                const ChunkRes &cr, int64_t slot) {
+    const StageHdr &h = S.h;
+    const int32_t i = cr.i;
+    if (slot + cr.r > P.q_cap) { raise_err(P.err, kErrIndex); return; }   // corrupt rows only
+    if (cr.fast) {
+        const int32_t *col = S.ci + (cr.a - h.ci_lo);
+        uint32_t resmask = cr.resmask;
+        while (resmask) {
+            const int t = __ffs(resmask) - 1;
+            resmask &= resmask - 1;
+            P.q[slot] = make_int2(i, col[t]);
+            if (kBatched) P.qk[slot] = h.k;
+            ++slot;
+        }
+    } else {
+        for (int32_t e = cr.a; e < cr.a_next; ++e) {
+            const int32_t j = (e >= h.ci_lo && e < h.ci_hi) ? S.ci[e - h.ci_lo] : __ldg(I.col_idx + e);
+            if ((uint32_t)j < (uint32_t)i && e != cr.mk && entry_open<kGen>(P, S, I, e, i, j)) {
+                P.q[slot] = make_int2(i, j);
                 if (kBatched) P.qk[slot] = h.k;
                 ++slot;
-            }
-        } else {
-            for (int32_t e = a; e < a_next; ++e) {
-                const int32_t j = (e >= h.ci_lo && e < h.ci_hi) ? S.ci[e - h.ci_lo] : __ldg(I.col_idx + e);
-                if ((uint32_t)j < (uint32_t)i && e != mk && entry_open<kGen>(P, S, I, e, i, j)) {
-                    P.q[slot] = make_int2(i, j);
-                    if (kBatched) P.qk[slot] = h.k;
-                    ++slot;
-                }
             }
         }
     }
@@ -407,11 +418,27 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
             tc.vis_lo = (int32_t)lo;
             tc.vis_hi = hi < lo ? -1 : (int32_t)hi;
         }
-#pragma unroll 1
-        for (int q = 0; q < kChunksPerConsumer; ++q) {
-            const int cc = warp * kChunksPerConsumer + q;
-            if (cc * kChunk >= S.h.ts) break;
-            init_consume_chunk<kBatched, kGen>(P, S, I, cc, lane, tc, &band_cnt, my_pairs);
+        static_assert(kChunksPerConsumer == 2, "a consumer warp scans two chunks per tile");
+        {
+            // both chunks are scanned first; their pairs then take one range of
+            // queue slots (one prefix sum and one band counter update per tile)
+            const int cc0 = warp * 2, cc1 = warp * 2 + 1;
+            ChunkRes c0, c1;
+            c0.r = c1.r = 0;
+            if (cc0 * kChunk < S.h.ts) init_scan_chunk<kBatched, kGen>(P, S, I, cc0, lane, tc, c0);
+            if (cc1 * kChunk < S.h.ts) init_scan_chunk<kBatched, kGen>(P, S, I, cc1, lane, tc, c1);
+            const int rr = c0.r + c1.r;
+            const int incl = warp_incl_scan(rr, lane);
+            const int total = __shfl_sync(kFull, incl, 31);
+            if (total > 0) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(&band_cnt, (unsigned long long)total);
+                base = __shfl_sync(kFull, base, 0);
+                if (lane == 0) my_pairs += (unsigned long long)total;
+                const int64_t slot = S.h.qband + (int64_t)base + (incl - rr);
+                if (c0.r > 0) init_emit_chunk<kBatched, kGen>(P, S, I, c0, slot);
+                if (c1.r > 0) init_emit_chunk<kBatched, kGen>(P, S, I, c1, slot + c0.r);
+            }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
