@@ -247,6 +247,7 @@ struct TileCtx {
     int32_t nbits;      // bits present in the stage
     int32_t vis_lo;     // instance-local tiles [vis_lo, vis_hi] are visible
     int32_t vis_hi;
+    bool staged;        // the stage holds the columns and bits of the tile's whole entry range
 };
 
 // One chunk of 32 sites. The tiles of this CTA's band that were finished at
@@ -257,6 +258,7 @@ struct TileCtx {
 // What the emission of a scanned chunk needs (per lane).
 struct ChunkRes {
     int32_t i, a, a_next, mk;
+    int32_t lab;        // label[i] to store (may be a load still in flight)
     uint32_t resmask;
     int32_t r;          // residual pairs of the lane's site
     bool fast;          // warp-uniform: the register path scanned the chunk
@@ -284,13 +286,11 @@ __device__ __forceinline__ void init_scan_chunk(const Params &P, const Stage &S,
         raise_err(P.err, kErrIndex);
         a = a_next = h.e0 > 0 ? h.e0 : 0;
     }
-    const int32_t beg = __shfl_sync(kFull, a, 0);
-    const int32_t end = __shfl_sync(kFull, a_next, 31);
+    // rows now lie inside [e0, e1]; tc.staged says whether the stage holds
+    // all of that range (columns and bits)
     const int32_t deg = a_next - a;
     const int32_t dmax = __reduce_max_sync(kFull, (uint32_t)deg);
-    const bool fast = dmax <= kRowRegs && beg >= h.ci_lo && end <= h.ci_hi && a >= beg &&
-                      a_next <= end && (kGen || (tc.rb0 + beg >= 0 && tc.rb0 + end <= tc.nbits));
-    const bool all_fast = __all_sync(kFull, fast);
+    const bool all_fast = dmax <= kRowRegs && tc.staged;
     int32_t m = INT32_MAX, cnt = 0;
     int32_t mk = -1;
     uint32_t resmask = 0;
@@ -325,13 +325,14 @@ __device__ __forceinline__ void init_scan_chunk(const Params &P, const Stage &S,
         scan_row_general<kGen>(P, S, I, a, a_next, i, m, mk, cnt, bad);
     }
     if (bad) raise_err(P.err, kErrIndex);
+    // the label; the caller stores it after scanning its other chunk, so the
+    // shortcut's load below has that scan's time to arrive
     int32_t lab = cnt ? m : i;
     if (cnt) {
         const int32_t mt = (int32_t)((uint32_t)m / kTileSites);
         if (mt >= tc.vis_lo && mt <= tc.vis_hi) lab = __ldcg(I.labels + m);
     }
-    if (i < n) I.labels[i] = lab;
-
+    cr.lab = lab;
     cr.i = i;
     cr.a = a;
     cr.a_next = a_next;
@@ -412,6 +413,8 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
         TileCtx tc;
         tc.rb0 = (int32_t)(I.bit_off - (S.h.w_lo << 5));
         tc.nbits = (int32_t)(32 * (S.h.w_hi - S.h.w_lo));
+        tc.staged = S.h.status == 0 && S.h.e0 >= S.h.ci_lo && S.h.e1 <= S.h.ci_hi &&
+                    (kGen || (tc.rb0 + S.h.e0 >= 0 && tc.rb0 + S.h.e1 <= tc.nbits));
         {
             const int64_t lo = max(band_lo, I.tile_begin) - I.tile_begin;
             const int64_t hi = tile - kStages - I.tile_begin;
@@ -425,8 +428,11 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
             const int cc0 = warp * 2, cc1 = warp * 2 + 1;
             ChunkRes c0, c1;
             c0.r = c1.r = 0;
-            if (cc0 * kChunk < S.h.ts) init_scan_chunk<kBatched, kGen>(P, S, I, cc0, lane, tc, c0);
-            if (cc1 * kChunk < S.h.ts) init_scan_chunk<kBatched, kGen>(P, S, I, cc1, lane, tc, c1);
+            const bool has0 = cc0 * kChunk < S.h.ts, has1 = cc1 * kChunk < S.h.ts;
+            if (has0) init_scan_chunk<kBatched, kGen>(P, S, I, cc0, lane, tc, c0);
+            if (has1) init_scan_chunk<kBatched, kGen>(P, S, I, cc1, lane, tc, c1);
+            if (has0 && c0.i < I.n) I.labels[c0.i] = c0.lab;
+            if (has1 && c1.i < I.n) I.labels[c1.i] = c1.lab;
             const int rr = c0.r + c1.r;
             const int incl = warp_incl_scan(rr, lane);
             const int total = __shfl_sync(kFull, incl, 31);
