@@ -676,39 +676,34 @@ __global__ void __launch_bounds__(256) k_reduce(Params P) {
             int32_t v[kRedSlots];
 #pragma unroll
             for (int u = 0; u < kRedSlots; ++u) {
-                if (st[u] == kTaskChase) v[u] = red_load(L[u] + a[u]);
-                else if (st[u] == kTaskRoot) v[u] = red_load(L[u] + b[u]);
-                else if (st[u] == kTaskMerge) v[u] = atomicMin(L[u] + a[u], b[u]);
-                else v[u] = 0;
+                int32_t *ptr = L[u] + (st[u] == kTaskRoot ? b[u] : a[u]);
+                v[u] = 0;
+                if (st[u] == kTaskMerge) v[u] = atomicMin(ptr, b[u]);
+                else if (st[u] != kTaskDone) v[u] = red_load(ptr);
             }
-            // use
+            // use: the next state of every slot by selects (no divergent paths)
             bool any = false;
 #pragma unroll
             for (int u = 0; u < kRedSlots; ++u) {
-                if (st[u] == kTaskChase) {
+                const int32_t y = v[u], A = a[u], Bv = b[u];
+                const int s = st[u];
 #ifdef CCL_DEVICE_STATS
-                    st_hops++;
+                st_hops += (s == kTaskChase || s == kTaskRoot);
+                st_atom += (s == kTaskMerge);
 #endif
-                    const int32_t y = v[u];
-                    if (y == a[u]) st[u] = P.link_mode ? kTaskMerge : kTaskRoot;
-                    else if (y == b[u]) st[u] = kTaskDone;
-                    else { a[u] = max(y, b[u]); b[u] = min(y, b[u]); }
-                } else if (st[u] == kTaskRoot) {
-#ifdef CCL_DEVICE_STATS
-                    st_hops++;
-#endif
-                    if (v[u] == b[u]) st[u] = kTaskMerge;
-                    else b[u] = v[u];
-                } else if (st[u] == kTaskMerge) {
-#ifdef CCL_DEVICE_STATS
-                    st_atom++;
-#endif
-                    // Algorithm 1's atomicMin outcome on label_1 = a > label_2 = b
-                    const int32_t old = v[u];
-                    if (old == b[u] || old == a[u]) st[u] = kTaskDone;
-                    else if (old > b[u]) a[u] = old;
-                    else { a[u] = b[u]; b[u] = old; }
-                }
+                const bool c_root = y == A, c_hit = y == Bv;
+                const int32_t ca = c_root ? A : max(y, Bv), cb = c_root ? Bv : min(y, Bv);
+                const int cs = c_root ? (P.link_mode ? kTaskMerge : kTaskRoot) : (c_hit ? kTaskDone : kTaskChase);
+                const bool r_root = y == Bv;
+                const int32_t rb = r_root ? Bv : y;
+                const int rs = r_root ? kTaskMerge : kTaskRoot;
+                const bool m_done = (y == Bv) || (y == A);
+                const bool m_gt = y > Bv;
+                const int32_t ma = m_gt ? y : Bv, mb = m_gt ? Bv : y;
+                const int ms = m_done ? kTaskDone : kTaskMerge;
+                a[u] = s == kTaskChase ? ca : (s == kTaskMerge ? ma : A);
+                b[u] = s == kTaskChase ? cb : (s == kTaskRoot ? rb : (s == kTaskMerge ? mb : Bv));
+                st[u] = s == kTaskChase ? cs : (s == kTaskRoot ? rs : (s == kTaskMerge ? ms : s));
                 any |= st[u] != kTaskDone;
             }
             if (!__any_sync(kFull, any || pf_ok) && (kStatic || nxt >= wlen)) break;
