@@ -309,7 +309,7 @@ def run_ours(args, rank, world, local):
     opts = {name: ccl.ccl_get_option(ctx, o) for name, o in (
         ("threads", ccl.CCL_OPT_BLOCK_THREADS), ("ctas_per_sm", ccl.CCL_OPT_CTAS_PER_SM),
         ("pre_analysis", ccl.CCL_OPT_PRE_ANALYSIS), ("link_mode", ccl.CCL_OPT_LINK_MODE),
-        ("refill", ccl.CCL_OPT_REFILL))}
+        ("refill", ccl.CCL_OPT_REFILL), ("analysis_order", ccl.CCL_OPT_ANALYSIS_ORDER))}
 
     def step():
         if kind == "csr":

@@ -89,10 +89,14 @@ typedef enum {
     CCL_OPT_LINK_MODE = 5,     /* step (iii): 0 (default) a root is linked under the other tree's
                                   root, as in Algorithm 1; 1 under the node the other chain has
                                   reached (same atomicMin loop, shorter walks on trees) */
-    CCL_OPT_REFILL = 6         /* step (iii): 1 (default) each thread serves a fixed stride of the
+    CCL_OPT_REFILL = 6,        /* step (iii): 1 (default) each thread serves a fixed stride of the
                                   residual pairs and loads its next one ahead; 0 a warp hands its
                                   pairs out in order to whichever threads are free (balances
                                   uneven chains) */
+    CCL_OPT_ANALYSIS_ORDER = 7 /* steps (ii)/(iv): 1 (default) each warp walks a contiguous range of
+                                  sites in increasing order (chains meet roots it already stored);
+                                  0 the sites are interleaved over the warps (balances inputs
+                                  without locality) */
 } ccl_option;
 
 CCL_API ccl_status ccl_set_option(ccl_context *ctx, int option, int64_t value);
@@ -287,7 +291,7 @@ CCL_API ccl_status ccl_get_step_times(ccl_context *ctx, float *ms, int32_t n);
 /*
  * ccl_autotune -- synchronous: times the labelling of the given instance under
  * candidate settings (analysis threads per CTA, step (ii) on/off, link mode,
- * refill mode)
+ * refill mode, analysis order)
  * and keeps the fastest for instances of this size class (log2 of the site
  * count, mean degree rounded); the choice also becomes the context's
  * options (ccl_get_option reports it). Every candidate writes the same labels,

@@ -36,6 +36,7 @@ CCL_OPT_PROFILE = 3
 CCL_OPT_CTAS_PER_SM = 4
 CCL_OPT_LINK_MODE = 5
 CCL_OPT_REFILL = 6
+CCL_OPT_ANALYSIS_ORDER = 7
 
 
 class CclError(RuntimeError):

@@ -30,6 +30,7 @@ struct TuneChoice {
     int pre_analysis = 1;
     int link_mode = 0;
     int refill = 1;         // step (iii): 1 static per-lane pairs, 0 in-order hand-out
+    int ana_seq = 1;        // steps (ii)/(iv): 1 contiguous ranges per warp, 0 interleaved
 };
 
 struct GraphEntry {
@@ -139,8 +140,8 @@ int blocks_per_sm(ccl_context *ctx, int kernel_id, int threads) {
     switch (kernel_id) {
         case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init<false>, kInitThreads, kInitSmem); break;
         case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init<true>, kInitThreads, kInitSmem); break;
-        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_analysis<false>, threads, 0); break;
-        case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_analysis<true>, threads, 0); break;
+        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_analysis<false, true>, threads, 0); break;
+        case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_analysis<true, true>, threads, 0); break;
         case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_reduce<false, true>, threads, 0); break;
         case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_reduce<true, true>, threads, 0); break;
         case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init<false, true>, kInitThreads, kInitSmem); break;
@@ -244,9 +245,18 @@ ccl_status enqueue_steps(ccl_context *ctx, const Params &P0, bool batched, const
     }
     CCL_CUDA(cudaGetLastError());
     if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[1], s));
+    auto analysis = [&]() {
+        const unsigned g = (unsigned)grid_for(ctx, batched ? 3 : 2, tc, warps_chunks);
+        if (batched) {
+            if (tc.ana_seq) k_analysis<true, true><<<g, T, 0, s>>>(P);
+            else k_analysis<true, false><<<g, T, 0, s>>>(P);
+        } else {
+            if (tc.ana_seq) k_analysis<false, true><<<g, T, 0, s>>>(P);
+            else k_analysis<false, false><<<g, T, 0, s>>>(P);
+        }
+    };
     if (tc.pre_analysis) {
-        if (batched) k_analysis<true><<<(unsigned)grid_for(ctx, 3, tc, warps_chunks), T, 0, s>>>(P);
-        else k_analysis<false><<<(unsigned)grid_for(ctx, 2, tc, warps_chunks), T, 0, s>>>(P);
+        analysis();
         CCL_CUDA(cudaGetLastError());
     }
     if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[2], s));
@@ -259,8 +269,7 @@ ccl_status enqueue_steps(ccl_context *ctx, const Params &P0, bool batched, const
     }
     CCL_CUDA(cudaGetLastError());
     if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[3], s));
-    if (batched) k_analysis<true><<<(unsigned)grid_for(ctx, 3, tc, warps_chunks), T, 0, s>>>(P);
-    else k_analysis<false><<<(unsigned)grid_for(ctx, 2, tc, warps_chunks), T, 0, s>>>(P);
+    analysis();
     CCL_CUDA(cudaGetLastError());
     if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[4], s));
     return CCL_OK;
@@ -274,7 +283,8 @@ uint64_t fnv1a(const void *data, size_t bytes, uint64_t h = 1469598103934665603u
 
 bool same_choice(const TuneChoice &a, const TuneChoice &b) {
     return a.threads == b.threads && a.ctas_per_sm == b.ctas_per_sm &&
-           a.pre_analysis == b.pre_analysis && a.link_mode == b.link_mode && a.refill == b.refill;
+           a.pre_analysis == b.pre_analysis && a.link_mode == b.link_mode && a.refill == b.refill &&
+           a.ana_seq == b.ana_seq;
 }
 
 GraphEntry *find_graph(ccl_context *ctx, const GraphEntry &key) {
@@ -600,10 +610,11 @@ ccl_status ccl_context_create(ccl_context **out, int device) {
     if (const char *env = getenv("CCL_TUNE_CACHE")) {
         if (FILE *f = fopen(env, "r")) {
             long long cls;
-            int a, b, c, d, r;
-            while (fscanf(f, "%lld %d %d %d %d %d", &cls, &a, &b, &c, &d, &r) == 6) {
+            int a, b, c, d, r, q;
+            while (fscanf(f, "%lld %d %d %d %d %d %d", &cls, &a, &b, &c, &d, &r, &q) == 7) {
                 TuneChoice t;
                 t.threads = a; t.ctas_per_sm = b; t.pre_analysis = c; t.link_mode = d; t.refill = r ? 1 : 0;
+                t.ana_seq = q ? 1 : 0;
                 if (t.threads >= 64 && t.threads <= 512 && t.threads % 32 == 0) ctx->tune_table[cls] = t;
             }
             fclose(f);
@@ -657,6 +668,7 @@ ccl_status ccl_set_option(ccl_context *ctx, int option, int64_t value) {
             break;
         case CCL_OPT_LINK_MODE: ctx->opt.link_mode = value ? 1 : 0; break;
         case CCL_OPT_REFILL: ctx->opt.refill = value ? 1 : 0; break;
+        case CCL_OPT_ANALYSIS_ORDER: ctx->opt.ana_seq = value ? 1 : 0; break;
         default: return CCL_ERR_INVALID_ARGUMENT;
     }
     // explicit options take effect over any tuned entry
@@ -674,6 +686,7 @@ ccl_status ccl_get_option(ccl_context *ctx, int option, int64_t *value) {
         case CCL_OPT_CTAS_PER_SM: *value = ctx->opt.ctas_per_sm; break;
         case CCL_OPT_LINK_MODE: *value = ctx->opt.link_mode; break;
         case CCL_OPT_REFILL: *value = ctx->opt.refill; break;
+        case CCL_OPT_ANALYSIS_ORDER: *value = ctx->opt.ana_seq; break;
         default: return CCL_ERR_INVALID_ARGUMENT;
     }
     return CCL_OK;
@@ -901,7 +914,6 @@ ccl_status ccl_label_host(ccl_context *ctx, int32_t n, int64_t nnz, const int32_
     if ((int64_t)need > ctx->host_in_cap) {
         CCL_CUDA(cudaStreamSynchronize(s));
         if (ctx->d_host_in) cudaFree(ctx->d_host_in);
-    if (ctx->d_aux) cudaFree(ctx->d_aux);
         ctx->d_host_in = nullptr;
         ctx->host_in_cap = 0;
         drop_graphs(ctx);    // graphs may hold pointers into the old buffer
@@ -995,11 +1007,13 @@ ccl_status ccl_autotune(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t 
     for (int T : {128, 256, 512})
         for (int pre = 0; pre < 2; ++pre)
             for (int lm = 0; lm < 2; ++lm)
-                for (int rf = 0; rf < 2; ++rf) {
-                    TuneChoice tc;
-                    tc.threads = T; tc.ctas_per_sm = 0; tc.pre_analysis = pre; tc.link_mode = lm; tc.refill = rf;
-                    cands.push_back(tc);
-                }
+                for (int rf = 0; rf < 2; ++rf)
+                    for (int sq = 0; sq < 2; ++sq) {
+                        TuneChoice tc;
+                        tc.threads = T; tc.ctas_per_sm = 0; tc.pre_analysis = pre; tc.link_mode = lm;
+                        tc.refill = rf; tc.ana_seq = sq;
+                        cands.push_back(tc);
+                    }
     for (const TuneChoice &tc : cands) {
         float tmin = 1e30f;
         for (int rep = 0; rep < 4 && st == CCL_OK; ++rep) {
@@ -1024,8 +1038,9 @@ ccl_status ccl_autotune(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t 
     if (const char *env = getenv("CCL_TUNE_CACHE")) {
         if (FILE *f = fopen(env, "w")) {
             for (auto &kv : ctx->tune_table)
-                fprintf(f, "%lld %d %d %d %d %d\n", (long long)kv.first, kv.second.threads,
-                        kv.second.ctas_per_sm, kv.second.pre_analysis, kv.second.link_mode, kv.second.refill);
+                fprintf(f, "%lld %d %d %d %d %d %d\n", (long long)kv.first, kv.second.threads,
+                        kv.second.ctas_per_sm, kv.second.pre_analysis, kv.second.link_mode, kv.second.refill,
+                        kv.second.ana_seq);
             fclose(f);
         }
     }

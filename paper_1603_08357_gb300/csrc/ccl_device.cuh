@@ -462,13 +462,24 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
 // A warp walks kAnaChunks chunks at once (one chain per lane per chunk) so
 // that their dependent loads overlap.
 
-template <bool kBatched>
+// kSeq = true: warp w walks a contiguous range of chunk groups in increasing
+// order, so the chains of its later sites run into roots it has already
+// stored (lattices numbered row by row) and, batched, the instance of a chunk
+// changes rarely. kSeq = false: groups are interleaved over the warps (grid
+// stride), which balances inputs without locality (randomly numbered trees).
+template <bool kBatched, bool kSeq>
 __global__ void __launch_bounds__(512) k_analysis(Params P) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t ngroups = (P.n_chunks + kAnaChunks - 1) / kAnaChunks;
-    for (int64_t gidx = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); gidx < ngroups;
-         gidx += nwarps) {
+    const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t per = kSeq ? (ngroups + nwarps - 1) / nwarps : 1;
+    const int64_t g0 = kSeq ? min(wid * per, ngroups) : wid;
+    const int64_t g1 = kSeq ? min(g0 + per, ngroups) : ngroups;
+    const int64_t gstep = kSeq ? 1 : nwarps;
+    int kc = 0;                          // cached instance and its chunk range
+    int64_t kc_lo = 0, kc_hi = kBatched ? 0 : P.n_chunks;
+    for (int64_t gidx = g0; gidx < g1; gidx += gstep) {
         int32_t *L[kAnaChunks];
         int32_t site[kAnaChunks], x[kAnaChunks], first[kAnaChunks];
         int32_t cap = 0;
@@ -480,8 +491,12 @@ __global__ void __launch_bounds__(512) k_analysis(Params P) {
             L[u] = nullptr;
             site[u] = 0;
             if (c < P.n_chunks) {
-                const int k = kBatched ? find_inst(P, c) : 0;
-                const Inst I = inst_of<kBatched>(P, k);
+                if (kBatched && (c < kc_lo || c >= kc_hi)) {
+                    kc = find_inst(P, c);
+                    kc_lo = P.insts[kc].chunk_begin;
+                    kc_hi = kc + 1 < P.K ? P.insts[kc + 1].chunk_begin : P.n_chunks;
+                }
+                const Inst I = inst_of<kBatched>(P, kc);
                 site[u] = (int32_t)((c - I.chunk_begin) * kChunk) + lane;
                 L[u] = I.labels;
                 cap = max(cap, I.n);

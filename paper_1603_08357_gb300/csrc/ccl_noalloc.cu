@@ -70,7 +70,7 @@ ccl_status setup_device(int dev, DeviceSetup **out) {
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.init_per_sm, k_init<false>, kInitThreads, kInitSmem);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.ana_per_sm, k_analysis<false>, 256, 0);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.ana_per_sm, k_analysis<false, true>, 256, 0);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.red_per_sm, k_reduce<false, true>, 256, 0);
         if (e != cudaSuccess) {
@@ -148,9 +148,9 @@ extern "C" ccl_status ccl_label_noalloc(int32_t n, int64_t nnz, const int32_t *r
     cudaError_t e = cudaMemsetAsync(d->scratch, 0, kOffBand + sizeof(BandRec) * (size_t)g_init, s);
     if (e == cudaSuccess) {
         k_init<false><<<(unsigned)g_init, kInitThreads, kInitSmem, s>>>(P);
-        k_analysis<false><<<(unsigned)g_ana, 256, 0, s>>>(P);
+        k_analysis<false, true><<<(unsigned)g_ana, 256, 0, s>>>(P);
         k_reduce<false, true><<<(unsigned)g_red, 256, 0, s>>>(P);
-        k_analysis<false><<<(unsigned)g_ana, 256, 0, s>>>(P);
+        k_analysis<false, true><<<(unsigned)g_ana, 256, 0, s>>>(P);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -126,3 +126,21 @@ def test_spanning_crossing_near_exact_threshold(ctx):
     x, err = P.crossing(ps, curves[0], curves[1], 1500)
     assert err is not None and 0 < err < 0.005
     assert x is not None and abs(x - pc) < 0.01, x
+
+
+def test_stats_after_host_path_grows(ctx):
+    """ccl_relabel and ccl_spanning keep working after the host-buffer entry
+    point has grown its device buffers on the same context."""
+    small = L.make_instance(dict(kind="triangle", L=64, p=0.5, seed=1, periodic_y=False))
+    lab = gpu_label(ctx, small)
+    d_lab = torch.from_numpy(lab).to(DEV)
+    seq = torch.empty(small.n, dtype=torch.int32, device=DEV)
+    nc = torch.zeros(1, dtype=torch.int32, device=DEV)
+    assert ccl.ccl_relabel(ctx, small.n, d_lab, seq, nc) == ccl.CCL_OK      # scratch allocated
+    big = L.make_instance(dict(kind="triangle", L=700, p=0.4, seed=2))
+    out = np.empty(big.n, np.int32)
+    assert ccl.ccl_label_host(ctx, big.n, big.nnz, big.row_ptr, big.col_idx, big.open_bits, out) == ccl.CCL_OK
+    assert np.array_equal(out, oracle.uf_label(big))
+    assert ccl.ccl_relabel(ctx, small.n, d_lab, seq, nc) == ccl.CCL_OK
+    assert ccl.ccl_sync(ctx) == ccl.CCL_OK
+    assert np.array_equal(seq.cpu().numpy(), stats.sequential(lab)[0])

@@ -97,11 +97,13 @@ def test_standard_bethe_has_no_residual_pairs(ctx, z, S):
 @pytest.mark.parametrize("pre", [0, 1])
 @pytest.mark.parametrize("link", [0, 1])
 @pytest.mark.parametrize("refill", [0, 1])
-def test_launch_options_same_labels(threads, pre, link, refill):
+@pytest.mark.parametrize("order", [0, 1])
+def test_launch_options_same_labels(threads, pre, link, refill, order):
     c = ccl.ccl_context_create(0)
     try:
         for opt, val in ((ccl.CCL_OPT_BLOCK_THREADS, threads), (ccl.CCL_OPT_PRE_ANALYSIS, pre),
                          (ccl.CCL_OPT_LINK_MODE, link), (ccl.CCL_OPT_REFILL, refill),
+                         (ccl.CCL_OPT_ANALYSIS_ORDER, order),
                          (ccl.CCL_OPT_CTAS_PER_SM, 1 if threads == 64 else 0)):
             assert ccl.ccl_set_option(c, opt, val) == ccl.CCL_OK
         lat = L.triangle(300, 0.52, 11)
@@ -266,7 +268,8 @@ def test_graph_replay_keyed_on_sizes(ctx):
 
 
 @pytest.mark.parametrize("refill", [0, 1])
-def test_refill_modes_on_uneven_work(refill):
+@pytest.mark.parametrize("order", [0, 1])
+def test_refill_modes_on_uneven_work(refill, order):
     """Both ways of handing residual pairs to threads, on inputs whose chains
     differ widely in length: a randomly numbered tree, a multigraph, and a
     batch of mixed instances."""
@@ -274,7 +277,8 @@ def test_refill_modes_on_uneven_work(refill):
     c = ccl.ccl_context_create(0)
     try:
         assert ccl.ccl_set_option(c, ccl.CCL_OPT_REFILL, refill) == ccl.CCL_OK
-        assert ccl.ccl_set_option(c, ccl.CCL_OPT_PRE_ANALYSIS, 0) == ccl.CCL_OK
+        assert ccl.ccl_set_option(c, ccl.CCL_OPT_PRE_ANALYSIS, 1) == ccl.CCL_OK
+        assert ccl.ccl_set_option(c, ccl.CCL_OPT_ANALYSIS_ORDER, order) == ccl.CCL_OK
         for lat in (L.cayley(3, 17, 0.5, 3, perm_seed=5), L.random_graph(50000, 90000, 4),
                     L.triangle(1000, 0.6, 3)):
             assert np.array_equal(gpu_label(c, lat), oracle.uf_label(lat))
