@@ -163,6 +163,8 @@ __device__ __forceinline__ void init_produce(const Params &P, Stage *st, uint64_
     cta_band(P.n_tiles, band_lo, band_hi);
     int64_t t_local = 0;
     int64_t qband = 0;
+    int kc = 0;                              // cached instance and its tile range
+    int64_t kc_lo = 0, kc_hi = kBatched ? 0 : P.n_tiles;
     for (int64_t tile = band_lo; tile < band_hi; ++tile, ++t_local) {
         const int s = (int)(t_local % kStages);
         const int64_t use = t_local / kStages;
@@ -170,7 +172,12 @@ __device__ __forceinline__ void init_produce(const Params &P, Stage *st, uint64_
             raise_err(P.err, kErrNonconv);
             break;
         }
-        const int k = kBatched ? find_inst_tile(P, tile) : 0;
+        if (kBatched && (tile < kc_lo || tile >= kc_hi)) {
+            kc = find_inst_tile(P, tile);
+            kc_lo = P.insts[kc].tile_begin;
+            kc_hi = kc + 1 < P.K ? P.insts[kc + 1].tile_begin : P.n_tiles;
+        }
+        const int k = kc;
         const Inst I = inst_of<kBatched>(P, k);
         StageHdr h;
         h.k = k;
