@@ -511,6 +511,11 @@ def run_batched(args, rank, world, local):
     labels = torch.empty(b.n_total, dtype=torch.int32, device=dev)
     ctx = ccl.ccl_context_create(local)
     stream = torch.cuda.current_stream(dev)
+    tuned = None
+    if not args.no_autotune:
+        st_t, best_ms = ccl.ccl_autotune_batched(ctx, b.k, b.site_off, b.ent_off, rp, ci, bits, labels, stream)
+        ccl.check(st_t, "ccl_autotune_batched")
+        tuned = {"best_ms": best_ms}
 
     def step():
         st = ccl.ccl_label_batched(ctx, b.k, b.site_off, b.ent_off, rp, ci, bits, labels, stream)
@@ -595,7 +600,7 @@ def run_batched(args, rank, world, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
             "config": {"workload": "batched", "instances": b.k, "n_sites": b.n_total, "nnz": b.nnz_total,
-                       "residual_pairs": q, "generation_s": t_gen,
+                       "residual_pairs": q, "generation_s": t_gen, "autotune": tuned,
                        "l2": "inputs larger than L2 (no flush)"},
             "one_at_a_time": {"ms_per_step": ms_one, "value": world * b.n_total / (ms_one / 1e3),
                               "calls_per_step": b.k, "speedup_batched": ms_one / ms,

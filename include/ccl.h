@@ -302,6 +302,20 @@ CCL_API ccl_status ccl_autotune(ccl_context *ctx, int32_t n_sites, int64_t nnz, 
                         const int32_t *col_idx, const uint32_t *open_bits, int32_t *labels,
                         void *stream, float *best_ms);
 
+/*
+ * ccl_autotune_batched -- ccl_autotune for ccl_label_batched: times one
+ * batched call of these K instances under each candidate setting (step (ii)
+ * on/off, link mode, refill mode, analysis order) and keeps the fastest for
+ * batches of this mean instance size and degree (a class of its own, apart
+ * from single instances). Arguments as ccl_label_batched; `labels` holds the
+ * correct result afterwards; best_ms (optional) receives the best time.
+ * Synchronous; each candidate runs three times, so budget ~50 calls.
+ */
+CCL_API ccl_status ccl_autotune_batched(ccl_context *ctx, int32_t n_inst, const int64_t *site_off,
+                                        const int64_t *ent_off, const int32_t *row_ptr,
+                                        const int32_t *col_idx, const uint32_t *open_bits,
+                                        int32_t *labels, void *stream, float *best_ms);
+
 /* ---------------------------------------------------------------------------
  * Request loop (continuous batching). A server thread admits submitted
  * requests while the device memory they need is free (free HBM minus a

@@ -103,6 +103,7 @@ def _load() -> ctypes.CDLL:
         "ccl_get_stats": (C, [P, ctypes.POINTER(ccl_run_stats)]),
         "ccl_get_step_times": (C, [P, ctypes.POINTER(ctypes.c_float), I32]),
         "ccl_autotune": (C, [P, I32, I64, P, P, P, P, P, ctypes.POINTER(ctypes.c_float)]),
+        "ccl_autotune_batched": (C, [P, I32, P, P, P, P, P, P, P, ctypes.POINTER(ctypes.c_float)]),
         "ccl_server_create": (C, [ctypes.POINTER(P), ctypes.POINTER(ccl_server_config)]),
         "ccl_server_submit": (C, [P, ctypes.POINTER(ccl_request), ctypes.POINTER(ctypes.c_uint64)]),
         "ccl_server_wait": (C, [P, ctypes.c_uint64, P, I64]),
@@ -357,6 +358,20 @@ def ccl_autotune(ctx, n_sites: int, nnz: int, row_ptr, col_idx, open_bits, label
                            _dev_ptr(col_idx, "col_idx", _i32()),
                            _dev_ptr(open_bits, "open_bits", _bits_dtypes()),
                            _dev_ptr(labels, "labels", _i32()), _stream(stream), ctypes.byref(best))
+    return st, float(best.value)
+
+
+def ccl_autotune_batched(ctx, n_inst: int, site_off, ent_off, row_ptr, col_idx, open_bits, labels,
+                         stream=None):
+    so = np.ascontiguousarray(site_off, dtype=np.int64)
+    eo = np.ascontiguousarray(ent_off, dtype=np.int64)
+    if so.size != n_inst + 1 or eo.size != n_inst + 1:
+        return CCL_ERR_INVALID_ARGUMENT, 0.0
+    best = ctypes.c_float(0)
+    st = _lib.ccl_autotune_batched(ctx, int(n_inst), so.ctypes.data, eo.ctypes.data,
+                                   _dev_ptr(row_ptr, "row_ptr", _i32()), _dev_ptr(col_idx, "col_idx", _i32()),
+                                   _dev_ptr(open_bits, "open_bits", _bits_dtypes()),
+                                   _dev_ptr(labels, "labels", _i32()), _stream(stream), ctypes.byref(best))
     return st, float(best.value)
 
 

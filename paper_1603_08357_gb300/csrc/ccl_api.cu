@@ -211,6 +211,53 @@ int64_t size_class(int64_t n, int64_t nnz) {
     return (int64_t)lg * 1024 + std::min<int64_t>(deg, 1023);
 }
 
+// Batched calls are keyed by their mean instance size and degree, in a range
+// of classes of their own (a batch of K instances of n sites and a single
+// instance of n sites behave differently).
+int64_t batch_class(int64_t n_tot, int64_t nnz_tot, int64_t K) {
+    const int64_t c = size_class(n_tot / std::max<int64_t>(K, 1), nnz_tot / std::max<int64_t>(K, 1));
+    return K > 1 ? (int64_t(1) << 30) + c : c;
+}
+
+// Times each candidate (first run untimed, then `reps` - 1 timed runs, the
+// fastest counted) and returns the best in best/best_t. The profiling events
+// are off meanwhile.
+template <typename Runner>
+ccl_status tune_over(ccl_context *ctx, cudaStream_t s, const std::vector<TuneChoice> &cands, int reps,
+                     TuneChoice &best, float &best_t, Runner runner) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    CCL_CUDA(cudaEventCreate(&a));
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return CCL_ERR_CUDA; }
+    const int saved_profile = ctx->profile;
+    ctx->profile = 0;
+    ccl_status st = CCL_OK;
+    for (const TuneChoice &tc : cands) {
+        float tmin = 1e30f;
+        for (int rep = 0; rep < reps && st == CCL_OK; ++rep) {
+            cudaError_t e = cudaEventRecord(a, s);
+            if (e == cudaSuccess) st = runner(tc);
+            if (e == cudaSuccess && st == CCL_OK) e = cudaEventRecord(b, s);
+            if (e == cudaSuccess && st == CCL_OK) e = cudaEventSynchronize(b);
+            if (e != cudaSuccess) st = cuda_status(e);
+            float t = 0;
+            if (st == CCL_OK) cudaEventElapsedTime(&t, a, b);
+            if (rep > 0) tmin = std::min(tmin, t);
+        }
+        if (st != CCL_OK) break;
+        if (tmin < best_t) { best_t = tmin; best = tc; }
+    }
+    ctx->profile = saved_profile;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return st;
+}
+
+TuneChoice choice_for_class(ccl_context *ctx, int64_t cls) {
+    auto it = ctx->tune_table.find(cls);
+    if (it != ctx->tune_table.end()) return it->second;
+    return ctx->opt;
+}
+
 TuneChoice choice_for(ccl_context *ctx, int64_t n, int64_t nnz) {
     auto it = ctx->tune_table.find(size_class(n, nnz));
     if (it != ctx->tune_table.end()) return it->second;
@@ -711,10 +758,11 @@ ccl_status ccl_label(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t *ro
     return label_single(ctx, n, nnz, row_ptr, col_idx, bits, labels, (cudaStream_t)stream, tc);
 }
 
-ccl_status ccl_label_batched(ccl_context *ctx, int32_t K, const int64_t *site_off,
-                             const int64_t *ent_off, const int32_t *row_ptr,
-                             const int32_t *col_idx, const uint32_t *bits, int32_t *labels,
-                             void *stream) {
+namespace {
+// ccl_label_batched with the launch settings given (tc) or looked up (null)
+ccl_status label_batched(ccl_context *ctx, int32_t K, const int64_t *site_off, const int64_t *ent_off,
+                         const int32_t *row_ptr, const int32_t *col_idx, const uint32_t *bits,
+                         int32_t *labels, void *stream, const TuneChoice *force_tc) {
     if (!ctx || K < 0) return CCL_ERR_INVALID_ARGUMENT;
     if (K == 0) { ctx->last = ccl_run_stats{}; return CCL_OK; }
     if (!site_off || !ent_off) return CCL_ERR_INVALID_ARGUMENT;
@@ -754,7 +802,7 @@ ccl_status ccl_label_batched(ccl_context *ctx, int32_t K, const int64_t *site_of
     DeviceGuard guard(ctx->device);
     ccl_status st = ensure_workspace(ctx, nnz_tot, K > 1);
     if (st != CCL_OK) return st;
-    const TuneChoice tc = choice_for(ctx, n_tot / K, nnz_tot / K);
+    const TuneChoice tc = force_tc ? *force_tc : choice_for_class(ctx, batch_class(n_tot, nnz_tot, K));
     Params P = base_params(ctx, tc);
     P.K = K;
     P.n_chunks = chunks;
@@ -768,6 +816,45 @@ ccl_status ccl_label_batched(ccl_context *ctx, int32_t K, const int64_t *site_of
     std::vector<int64_t> offs(site_off, site_off + K + 1);
     offs.insert(offs.end(), ent_off, ent_off + K + 1);
     return run(ctx, P, true, tc, (cudaStream_t)stream, &table, h, true, &offs);
+}
+}  // namespace
+
+ccl_status ccl_label_batched(ccl_context *ctx, int32_t K, const int64_t *site_off,
+                             const int64_t *ent_off, const int32_t *row_ptr,
+                             const int32_t *col_idx, const uint32_t *bits, int32_t *labels,
+                             void *stream) {
+    return label_batched(ctx, K, site_off, ent_off, row_ptr, col_idx, bits, labels, stream, nullptr);
+}
+
+ccl_status ccl_autotune_batched(ccl_context *ctx, int32_t K, const int64_t *site_off,
+                                const int64_t *ent_off, const int32_t *row_ptr, const int32_t *col_idx,
+                                const uint32_t *bits, int32_t *labels, void *stream, float *best_ms) {
+    if (!ctx || K < 0) return CCL_ERR_INVALID_ARGUMENT;
+    if (K == 0) return CCL_OK;
+    if (!site_off || !ent_off) return CCL_ERR_INVALID_ARGUMENT;
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<TuneChoice> cands;
+    for (int pre = 0; pre < 2; ++pre)
+        for (int lm = 0; lm < 2; ++lm)
+            for (int rf = 0; rf < 2; ++rf)
+                for (int sq = 0; sq < 2; ++sq) {
+                    TuneChoice tc;
+                    tc.threads = 256; tc.ctas_per_sm = 0; tc.pre_analysis = pre; tc.link_mode = lm;
+                    tc.refill = rf; tc.ana_seq = sq;
+                    cands.push_back(tc);
+                }
+    TuneChoice best = ctx->opt;
+    float best_t = 1e30f;
+    ccl_status st = tune_over(ctx, s, cands, 3, best, best_t, [&](const TuneChoice &tc) {
+        return label_batched(ctx, K, site_off, ent_off, row_ptr, col_idx, bits, labels, stream, &tc);
+    });
+    if (st != CCL_OK) return st;
+    const int64_t n_tot = site_off[K], nnz_tot = ent_off[K];
+    ctx->tune_table[batch_class(n_tot, nnz_tot, K)] = best;
+    if (best_ms) *best_ms = best_t;
+    // leave the correct labels with the chosen settings
+    return label_batched(ctx, K, site_off, ent_off, row_ptr, col_idx, bits, labels, stream, &best);
 }
 
 ccl_status ccl_label_random(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
@@ -996,11 +1083,6 @@ ccl_status ccl_autotune(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t 
     if (st != CCL_OK || n == 0) return st;
     DeviceGuard guard(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
-    cudaEvent_t a, b;
-    CCL_CUDA(cudaEventCreate(&a));
-    CCL_CUDA(cudaEventCreate(&b));
-    const int saved_profile = ctx->profile;
-    ctx->profile = 0;
     TuneChoice best = ctx->opt;
     float best_t = 1e30f;
     std::vector<TuneChoice> cands;
@@ -1014,24 +1096,9 @@ ccl_status ccl_autotune(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t 
                         tc.refill = rf; tc.ana_seq = sq;
                         cands.push_back(tc);
                     }
-    for (const TuneChoice &tc : cands) {
-        float tmin = 1e30f;
-        for (int rep = 0; rep < 4 && st == CCL_OK; ++rep) {
-            cudaError_t e = cudaEventRecord(a, s);
-            if (e == cudaSuccess) st = label_single(ctx, n, nnz, row_ptr, col_idx, bits, labels, s, tc);
-            if (e == cudaSuccess && st == CCL_OK) e = cudaEventRecord(b, s);
-            if (e == cudaSuccess && st == CCL_OK) e = cudaEventSynchronize(b);
-            if (e != cudaSuccess) st = cuda_status(e);
-            float t = 0;
-            if (st == CCL_OK) cudaEventElapsedTime(&t, a, b);
-            if (rep > 0) tmin = std::min(tmin, t);
-        }
-        if (st != CCL_OK) break;
-        if (tmin < best_t) { best_t = tmin; best = tc; }
-    }
-    ctx->profile = saved_profile;
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
+    st = tune_over(ctx, s, cands, 4, best, best_t, [&](const TuneChoice &tc) {
+        return label_single(ctx, n, nnz, row_ptr, col_idx, bits, labels, s, tc);
+    });
     if (st != CCL_OK) return st;
     ctx->tune_table[size_class(n, nnz)] = best;
     ctx->opt = best;     // also the default for other size classes

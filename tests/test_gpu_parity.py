@@ -291,3 +291,26 @@ def test_refill_modes_on_uneven_work(refill, order):
         assert v == refill
     finally:
         ccl.ccl_context_destroy(c)
+
+
+def test_autotune_batched_keeps_labels_and_tunes_its_class():
+    from ccl_testutil import batch_to_dev
+    c = ccl.ccl_context_create(0)
+    try:
+        b = L.make_batch(L.batched_mix_specs(24, seed=31))
+        rp, ci, bits = batch_to_dev(b)
+        out = torch.full((b.n_total,), -1, dtype=torch.int32, device=DEV)
+        st, best = ccl.ccl_autotune_batched(c, b.k, b.site_off, b.ent_off, rp, ci, bits, out)
+        assert st == ccl.CCL_OK and best > 0
+        assert ccl.ccl_sync(c) == ccl.CCL_OK
+        got = out.cpu().numpy()
+        for k in range(b.k):
+            s0, s1 = int(b.site_off[k]), int(b.site_off[k + 1])
+            assert np.array_equal(got[s0:s1], oracle.uf_label(b.instance(k)))
+        out.fill_(-1)
+        assert ccl.ccl_label_batched(c, b.k, b.site_off, b.ent_off, rp, ci, bits, out) == ccl.CCL_OK
+        assert ccl.ccl_sync(c) == ccl.CCL_OK
+        assert np.array_equal(out.cpu().numpy(), got)
+        assert ccl.ccl_autotune_batched(c, 0, [0], [0], rp, ci, bits, out)[0] == ccl.CCL_OK
+    finally:
+        ccl.ccl_context_destroy(c)
