@@ -6,6 +6,10 @@ compared site by site with the oracle's union-find labels.
   triangle 4096x4096 (16,777,216 sites), p = 0.3473
   Bethe z=3, 24 shells, random position (50,331,646 sites), p = 0.5
   triangle 16384x16384 (268,435,456 sites), p = 0.3473  (the largest served instance)
+
+plus the largest input the int32 CSR allows: a triangle lattice whose
+2,147,344,344 entries sit just under 2^31 - 1 (every entry, slot and bit
+index near the top of its range).
 """
 import numpy as np
 import pytest
@@ -43,3 +47,21 @@ def test_full_size_matches_oracle(ctx, name):
     if lat.kind == "cayley":
         # forest identity at full size: clusters = sites - open bonds
         assert np.count_nonzero(got == np.arange(lat.n)) == lat.n - lat.n_open_bonds
+
+
+def test_maximum_csr_size(ctx):
+    """Triangle 18918 x 18918: 357,890,724 sites and 6 L^2 = 2,147,344,344 CSR
+    entries, the largest triangle lattice whose entry count fits int32."""
+    Ls = 18918
+    assert 6 * Ls * Ls < 2**31 - 1 < 6 * (Ls + 1) ** 2
+    lat = L.triangle(Ls, 0.3473, 7)
+    rp, ci, bits = to_dev(lat)
+    out = torch.full((lat.n,), -1, dtype=torch.int32, device=DEV)
+    assert ccl.ccl_label(ctx, lat.n, lat.nnz, rp, ci, bits, out) == ccl.CCL_OK
+    assert ccl.ccl_sync(ctx) == ccl.CCL_OK
+    got = out.cpu().numpy()
+    assert ccl.ccl_get_stats(ctx).nnz == lat.nnz
+    del rp, ci, bits, out
+    torch.cuda.empty_cache()
+    want = oracle.uf_label(lat)
+    assert np.array_equal(got, want), int(np.count_nonzero(got != want))
