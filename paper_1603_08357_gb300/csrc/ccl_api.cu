@@ -147,6 +147,8 @@ int blocks_per_sm(ccl_context *ctx, int kernel_id, int threads) {
         case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init<false, true>, kInitThreads, kInitSmem); break;
         case 7: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init_dense<false>, kDenseThreads, 0); break;
         case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init_dense<true>, kDenseThreads, 0); break;
+        case 9: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init_dense_tma<false>, kInitThreads, kDenseSmem); break;
+        case 10: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init_dense_tma<true>, kInitThreads, kDenseSmem); break;
         default: break;
     }
     if (e != cudaSuccess || nb < 1) { (void)cudaGetLastError(); nb = 1; }
@@ -273,14 +275,19 @@ ccl_status enqueue_steps(ccl_context *ctx, const Params &P0, bool batched, const
     Params P = P0;
     const bool dense = P.dense != 0;
     const bool gen = P.gen_thr != kNoGen;
-    const int64_t g_init = dense ? grid_init(ctx, gen ? 8 : 7, kDenseThreads, P.n_tiles)
-                                 : grid_init(ctx, batched ? 1 : (gen ? 6 : 0), kInitThreads, P.n_tiles);
+    const bool dense_tma = dense && P.nn_width <= kRowRegs;
+    const int64_t g_init = dense_tma ? grid_init(ctx, gen ? 10 : 9, kInitThreads, P.n_tiles)
+                           : dense ? grid_init(ctx, gen ? 8 : 7, kDenseThreads, P.n_tiles)
+                                   : grid_init(ctx, batched ? 1 : (gen ? 6 : 0), kInitThreads, P.n_tiles);
     P.n_bands = (int32_t)g_init;
     const int64_t g_red = (int64_t)ctx->num_sms * blocks_per_sm(ctx, batched ? 5 : 4, 256);
     CCL_CUDA(cudaMemsetAsync(P.counters, 0, 4 * sizeof(unsigned long long), s));
     CCL_CUDA(cudaMemsetAsync(P.band, 0, (size_t)g_init * sizeof(BandRec), s));
     if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[0], s));
-    if (dense) {
+    if (dense_tma) {
+        if (gen) k_init_dense_tma<true><<<(unsigned)g_init, kInitThreads, kDenseSmem, s>>>(P);
+        else k_init_dense_tma<false><<<(unsigned)g_init, kInitThreads, kDenseSmem, s>>>(P);
+    } else if (dense) {
         if (gen) k_init_dense<true><<<(unsigned)g_init, kDenseThreads, 0, s>>>(P);
         else k_init_dense<false><<<(unsigned)g_init, kDenseThreads, 0, s>>>(P);
     } else if (batched) {
@@ -381,8 +388,8 @@ bool stream_capturing(cudaStream_t s) {
 ccl_status run(ccl_context *ctx, Params P, bool batched, const TuneChoice &tc, cudaStream_t s,
                const std::vector<Inst> *table, uint64_t shape_hash, bool allow_graph = true,
                const std::vector<int64_t> *offsets = nullptr) {
-    for (int kid = 0; kid < 9; ++kid)
-        (void)blocks_per_sm(ctx, kid, kid >= 7 ? kDenseThreads
+    for (int kid = 0; kid < 11; ++kid)
+        (void)blocks_per_sm(ctx, kid, kid >= 9 ? kInitThreads : kid >= 7 ? kDenseThreads
                                                : (kid < 2 || kid == 6) ? kInitThreads : (kid >= 4 ? 256 : tc.threads));
     ctx->last.used_graph = 0;
     const bool capturing = stream_capturing(s);
@@ -649,6 +656,12 @@ ccl_status ccl_context_create(ccl_context **out, int device) {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_init<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kInitSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_init_dense_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kDenseSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_init_dense_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kDenseSmem);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         ccl_context_destroy(ctx);

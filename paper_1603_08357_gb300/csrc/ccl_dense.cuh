@@ -185,4 +185,267 @@ __global__ void __launch_bounds__(kDenseThreads) k_init_dense(Params P) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Dense list through the step-(i) pipeline of k_init: for lists of at most
+// kRowRegs slots, a producer lane streams each 1024-site tile's W slot slabs
+// (slot k: the tile's sites' entries nn[s0 + k*N ...], contiguous) and their
+// bit words into a 3-stage shared-memory ring with bulk asynchronous copies;
+// 16 consumer warps scan two 32-site chunks each, store labels after both are
+// scanned (the band shortcut's load overlaps the second scan) and append the
+// residual pairs of both through one prefix sum.
+
+constexpr int kDenseSlab = kTileSites + 8;        // a slot's slab, + 16-byte rounding
+constexpr int kDenseWords = kTileSites / 32 + 8;  // its bit words, + rounding
+
+struct __align__(16) DenseStageHdr {
+    int2 off[kRowRegs];        // staged tiles: slab[k] index and bw[k] bit index of site s0
+    int64_t nn_lo[kRowRegs];   // element of nn held at slab[k][0]
+    int64_t w_lo[kRowRegs];    // word of the bit array held at bw[k][0]
+    int32_t nn_cnt[kRowRegs];  // elements held
+    int32_t w_cnt[kRowRegs];   // words held
+    int64_t qband;             // first queue slot of the CTA's band
+    int32_t s0, ts;            // first site and sites of the tile
+    int32_t staged;            // 1: every slab and its bits are held whole
+    int32_t pad_;
+};
+
+struct __align__(16) DenseStage {
+    DenseStageHdr h;
+    int32_t nn[kRowRegs][kDenseSlab];
+    uint32_t bw[kRowRegs][kDenseWords];
+};
+
+constexpr size_t kDenseSmem = 64 + sizeof(DenseStage) * kStages;
+
+template <bool kGen>
+__device__ __forceinline__ void dense_produce(const Params &P, DenseStage *st, uint64_t *full, uint64_t *empty) {
+    int64_t band_lo, band_hi;
+    cta_band(P.n_tiles, band_lo, band_hi);
+    const int64_t n = P.one.n;
+    const int W = (int)P.nn_width;
+    const int64_t n_words = ((int64_t)W * n + 31) >> 5;
+    const int32_t *nn_end = P.nn + (int64_t)W * n;
+    const uint32_t *bits_end = kGen ? nullptr : P.one.bits + n_words;
+    const int64_t qband = min(band_lo * kTileSites, n) * W;
+    if (band_lo < band_hi) P.band[blockIdx.x].qbase = qband;
+    int64_t t_local = 0;
+    for (int64_t tile = band_lo; tile < band_hi; ++tile, ++t_local) {
+        const int s = (int)(t_local % kStages);
+        const int64_t use = t_local / kStages;
+        if (use > 0 && !mbar_wait_bounded(&empty[s], (uint32_t)((use - 1) & 1))) {
+            raise_err(P.err, kErrNonconv);
+            break;
+        }
+        DenseStageHdr &h = st[s].h;
+        const int64_t s0 = tile * kTileSites;
+        const int64_t ts = min((int64_t)kTileSites, n - s0);
+        h.s0 = (int32_t)s0;
+        h.ts = (int32_t)ts;
+        h.qband = qband;
+        uint32_t bytes = 0;
+        int staged = 1;
+        for (int k = 0; k < W; ++k) {
+            const int64_t e0 = s0 + (int64_t)k * n, e1 = e0 + ts;
+            int64_t lo, hi;
+            copy_window(P.nn, e0, e1, P.nn, nn_end, kDenseSlab, lo, hi);
+            h.nn_lo[k] = lo;
+            h.nn_cnt[k] = (int32_t)(hi - lo);
+            staged &= lo <= e0 && hi >= e1;
+            bytes += 4u * (uint32_t)(hi - lo);
+            if (!kGen) {
+                const int64_t w0 = e0 >> 5, w1 = ((e1 - 1) >> 5) + 1;
+                copy_window(P.one.bits, w0, w1, P.one.bits, bits_end, kDenseWords, lo, hi);
+                h.w_lo[k] = lo;
+                h.w_cnt[k] = (int32_t)(hi - lo);
+                staged &= lo <= w0 && hi >= w1;
+                bytes += 4u * (uint32_t)(hi - lo);
+            }
+        }
+        h.staged = staged;
+        if (staged)
+            for (int k = 0; k < W; ++k) {
+                const int64_t e0 = s0 + (int64_t)k * n;
+                h.off[k] = make_int2((int32_t)(e0 - h.nn_lo[k]), kGen ? 0 : (int32_t)(e0 - 32 * h.w_lo[k]));
+            }
+        mbar_arrive_expect_tx(&full[s], bytes);
+        for (int k = 0; k < W; ++k) {
+            if (h.nn_cnt[k]) bulk_g2s(st[s].nn[k], P.nn + h.nn_lo[k], 4u * (uint32_t)h.nn_cnt[k], &full[s]);
+            if (!kGen && h.w_cnt[k])
+                bulk_g2s(st[s].bw[k], P.one.bits + h.w_lo[k], 4u * (uint32_t)h.w_cnt[k], &full[s]);
+        }
+    }
+}
+
+// one lane's site of a staged chunk: slot k's neighbour and its open bit
+template <bool kGen>
+__device__ __forceinline__ void dense_slot(const Params &P, const DenseStage &S, int k, int64_t e, int32_t i,
+                                           int32_t &j, bool &open) {
+    const DenseStageHdr &h = S.h;
+    const int64_t r = e - h.nn_lo[k];
+    j = (r >= 0 && r < h.nn_cnt[k]) ? S.nn[k][r] : __ldg(P.nn + e);
+    if (kGen) {
+        open = j >= 0 && j < i && gen_bond_open(P.gen_seed, P.gen_thr, (uint32_t)j, (uint32_t)i);
+    } else {
+        const int64_t w = (e >> 5) - h.w_lo[k];
+        const uint32_t word = (w >= 0 && w < h.w_cnt[k]) ? S.bw[k][w] : __ldg(P.one.bits + (e >> 5));
+        open = (word >> (e & 31)) & 1u;
+    }
+}
+
+struct DenseChunk {
+    int32_t i, lab, m;
+    uint32_t lowmask;       // open lower slots
+    int32_t mk, r;
+};
+
+template <bool kGen>
+__device__ __forceinline__ void dense_scan_chunk(const Params &P, const DenseStage &S, int cc, int lane,
+                                                 const TileCtx &tc, DenseChunk &c) {
+    const DenseStageHdr &h = S.h;
+    const int64_t n = P.one.n;
+    const int W = (int)P.nn_width;
+    const int32_t loc = cc * kChunk + lane;
+    const int32_t i = h.s0 + loc;
+    const bool live = loc < h.ts;
+    int32_t m = INT32_MAX, mk = 0;
+    uint32_t lowmask = 0;
+    bool bad = false;
+    if (tc.staged) {
+#pragma unroll
+        for (int k = 0; k < kRowRegs; ++k) {
+            if (k >= W) break;
+            const int2 off = h.off[k];
+            const int32_t j = live ? S.nn[k][off.x + loc] : -1;
+            bool open;
+            if (kGen) {
+                open = (uint32_t)j < (uint32_t)i &&
+                       gen_bond_open(P.gen_seed, P.gen_thr, (uint32_t)j, (uint32_t)i);
+            } else {
+                const int32_t b = off.y + loc;
+                open = (S.bw[k][b >> 5] >> (b & 31)) & 1u;
+            }
+            bad |= (uint32_t)(j + 1) > (uint32_t)n;        // j < -1 or j >= n
+            if (open && (uint32_t)j < (uint32_t)i) {         // 0 <= j < i
+                lowmask |= 1u << k;
+                if (j < m) { m = j; mk = k; }
+            }
+        }
+    } else {
+        for (int k = 0; k < W; ++k) {
+            int32_t j = -1;
+            bool open = false;
+            if (live) dense_slot<kGen>(P, S, k, (int64_t)i + (int64_t)k * n, i, j, open);
+            bad |= j < -1 || (int64_t)j >= n;
+            if (j >= 0 && j < i && open) {
+                lowmask |= 1u << k;
+                if (j < m) { m = j; mk = k; }
+            }
+        }
+    }
+    if (bad) raise_err(P.err, kErrIndex);
+    const int cnt = __popc(lowmask);
+    int32_t lab = cnt ? m : i;
+    if (cnt) {
+        const int32_t mt = (int32_t)((uint32_t)m / kTileSites);
+        if (mt >= tc.vis_lo && mt <= tc.vis_hi) lab = __ldcg(P.one.labels + m);
+    }
+    c.i = i;
+    c.lab = lab;
+    c.m = m;
+    c.mk = mk;
+    c.lowmask = cnt ? (lowmask & ~(1u << mk)) : 0u;
+    c.r = cnt > 1 ? cnt - 1 : 0;
+}
+
+template <bool kGen>
+__device__ __forceinline__ void dense_emit_chunk(const Params &P, const DenseStage &S, const DenseChunk &c,
+                                                 bool staged, int64_t slot) {
+    const int64_t n = P.one.n;
+    const int32_t loc = c.i - S.h.s0;
+    uint32_t rm = c.lowmask;
+    while (rm) {
+        const int k = __ffs(rm) - 1;
+        rm &= rm - 1;
+        int32_t j;
+        if (staged) {
+            j = S.nn[k][S.h.off[k].x + loc];
+        } else {
+            bool open;
+            dense_slot<kGen>(P, S, k, (int64_t)c.i + (int64_t)k * n, c.i, j, open);
+        }
+        P.q[slot++] = make_int2(c.i, j);
+    }
+}
+
+template <bool kGen>
+__global__ void __launch_bounds__(kInitThreads, 2) k_init_dense_tma(Params P) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
+    uint64_t *empty = full + kStages;
+    DenseStage *st = reinterpret_cast<DenseStage *>(smem_raw + 64);
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kInitConsumers);
+        }
+        mbar_fence_init();
+    }
+    __shared__ unsigned long long band_cnt;
+    if (threadIdx.x == 0) band_cnt = 0;
+    __syncthreads();
+    if (warp == kInitConsumers) {
+        if (lane == 0) dense_produce<kGen>(P, st, full, empty);
+        return;
+    }
+    unsigned long long my_pairs = 0;
+    int64_t band_lo, band_hi;
+    cta_band(P.n_tiles, band_lo, band_hi);
+    int64_t t_local = 0;
+    for (int64_t tile = band_lo; tile < band_hi; ++tile, ++t_local) {
+        const int s = (int)(t_local % kStages);
+        if (!mbar_wait_bounded(&full[s], (uint32_t)((t_local / kStages) & 1))) {
+            raise_err(P.err, kErrNonconv);
+            break;
+        }
+        const DenseStage &S = st[s];
+        TileCtx tc;
+        tc.rb0 = 0;
+        tc.nbits = 0;
+        tc.staged = S.h.staged != 0;
+        {
+            const int64_t hi = tile - kStages;
+            tc.vis_lo = (int32_t)band_lo;
+            tc.vis_hi = hi < band_lo ? -1 : (int32_t)hi;
+        }
+        const int cc0 = warp * 2, cc1 = warp * 2 + 1;
+        DenseChunk c0, c1;
+        c0.r = c1.r = 0;
+        const bool has0 = cc0 * kChunk < S.h.ts, has1 = cc1 * kChunk < S.h.ts;
+        if (has0) dense_scan_chunk<kGen>(P, S, cc0, lane, tc, c0);
+        if (has1) dense_scan_chunk<kGen>(P, S, cc1, lane, tc, c1);
+        if (has0 && c0.i < P.one.n) P.one.labels[c0.i] = c0.lab;
+        if (has1 && c1.i < P.one.n) P.one.labels[c1.i] = c1.lab;
+        const int rr = c0.r + c1.r;
+        const int incl = warp_incl_scan(rr, lane);
+        const int total = __shfl_sync(kFull, incl, 31);
+        if (total > 0) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&band_cnt, (unsigned long long)total);
+            base = __shfl_sync(kFull, base, 0);
+            if (lane == 0) my_pairs += (unsigned long long)total;
+            const int64_t slot = S.h.qband + (int64_t)base + (incl - rr);
+            if (c0.r > 0) dense_emit_chunk<kGen>(P, S, c0, tc.staged, slot);
+            if (c1.r > 0) dense_emit_chunk<kGen>(P, S, c1, tc.staged, slot + c0.r);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+    }
+    if (lane == 0 && my_pairs) {
+        atomicAdd(P.counters, my_pairs);
+        atomicAdd(&P.band[blockIdx.x].cnt, my_pairs);
+    }
+}
+
 }  // namespace ccl
