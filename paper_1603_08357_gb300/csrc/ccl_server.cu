@@ -22,6 +22,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -475,8 +476,11 @@ ccl_status ccl_server_create(ccl_server **out, const ccl_server_config *cfg_in) 
     }
     S->slot_busy.assign(S->streams.size(), false);
     {
+        // copy threads: CCL_SERVER_COPY_THREADS, else three quarters of the host's cores, at most 12
         const unsigned hw = std::max(2u, std::thread::hardware_concurrency());
-        S->copier.reset(new CopyPool((int)std::min(8u, hw / 2)));
+        int nt = (int)std::min(12u, hw * 3 / 4);
+        if (const char *env = getenv("CCL_SERVER_COPY_THREADS")) nt = std::max(0, std::min(64, atoi(env)));
+        S->copier.reset(new CopyPool(nt));
     }
     S->th = std::thread(server_loop, S);
     *out = S;
