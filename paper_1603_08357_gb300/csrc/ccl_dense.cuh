@@ -373,7 +373,7 @@ __device__ __forceinline__ void dense_emit_chunk(const Params &P, const DenseSta
             bool open;
             dense_slot<kGen>(P, S, k, (int64_t)c.i + (int64_t)k * n, c.i, j, open);
         }
-        P.q[slot++] = make_int2(c.i, j);
+        P.q[slot++] = make_int2(c.lab, j);      // (parent of i, j): see init_emit_chunk
     }
 }
 

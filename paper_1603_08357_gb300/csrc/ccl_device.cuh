@@ -350,11 +350,15 @@ __device__ __forceinline__ void init_scan_chunk(const Params &P, const Stage &S,
 }
 
 // Writes the residual pairs of one scanned chunk from queue slot `slot` on.
+// A pair {i, j} is stored as (label[i], j): label[i] is i's parent in the
+// label forest and, i not being a root, step (iii) never rewrites it, so the
+// pair joins the same two trees and its root search starts one hop higher.
 template <bool kBatched, bool kGen = false>
 __device__ __forceinline__ void init_emit_chunk(const Params &P, const Stage &S, const Inst &I,
                                                 const ChunkRes &cr, int64_t slot) {
     const StageHdr &h = S.h;
     const int32_t i = cr.i;
+    const int32_t up = cr.lab;
     if (slot + cr.r > P.q_cap) { raise_err(P.err, kErrIndex); return; }   // corrupt rows only
     if (cr.fast) {
         const int32_t *col = S.ci + (cr.a - h.ci_lo);
@@ -362,7 +366,7 @@ __device__ __forceinline__ void init_emit_chunk(const Params &P, const Stage &S,
         while (resmask) {
             const int t = __ffs(resmask) - 1;
             resmask &= resmask - 1;
-            P.q[slot] = make_int2(i, col[t]);
+            P.q[slot] = make_int2(up, col[t]);
             if (kBatched) P.qk[slot] = h.k;
             ++slot;
         }
@@ -370,7 +374,7 @@ __device__ __forceinline__ void init_emit_chunk(const Params &P, const Stage &S,
         for (int32_t e = cr.a; e < cr.a_next; ++e) {
             const int32_t j = (e >= h.ci_lo && e < h.ci_hi) ? S.ci[e - h.ci_lo] : __ldg(I.col_idx + e);
             if ((uint32_t)j < (uint32_t)i && e != cr.mk && entry_open<kGen>(P, S, I, e, i, j)) {
-                P.q[slot] = make_int2(i, j);
+                P.q[slot] = make_int2(up, j);
                 if (kBatched) P.qk[slot] = h.k;
                 ++slot;
             }
