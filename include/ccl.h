@@ -297,6 +297,10 @@ CCL_API ccl_status ccl_get_step_times(ccl_context *ctx, float *ms, int32_t n);
  * options (ccl_get_option reports it). Every candidate writes the same labels,
  * so `labels` holds the correct result afterwards. best_ms (optional)
  * receives the best time.
+ * If the environment variable CCL_TUNE_CACHE names a file, ccl_autotune
+ * writes the context's whole table there (one line per size class: class,
+ * threads, CTAs per SM, step (ii), link mode, refill mode, analysis order)
+ * and ccl_context_create reads it back; lines that do not parse are ignored.
  */
 CCL_API ccl_status ccl_autotune(ccl_context *ctx, int32_t n_sites, int64_t nnz, const int32_t *row_ptr,
                         const int32_t *col_idx, const uint32_t *open_bits, int32_t *labels,

@@ -669,12 +669,14 @@ ccl_status ccl_context_create(ccl_context **out, int device) {
     }
     if (const char *env = getenv("CCL_TUNE_CACHE")) {
         if (FILE *f = fopen(env, "r")) {
-            long long cls;
-            int a, b, c, d, r, q;
-            while (fscanf(f, "%lld %d %d %d %d %d %d", &cls, &a, &b, &c, &d, &r, &q) == 7) {
+            char line[256];
+            while (fgets(line, sizeof line, f)) {     // a line that does not parse is skipped
+                long long cls;
+                int a, b, c, d, r, q;
+                if (sscanf(line, "%lld %d %d %d %d %d %d", &cls, &a, &b, &c, &d, &r, &q) != 7) continue;
                 TuneChoice t;
-                t.threads = a; t.ctas_per_sm = b; t.pre_analysis = c; t.link_mode = d; t.refill = r ? 1 : 0;
-                t.ana_seq = q ? 1 : 0;
+                t.threads = a; t.ctas_per_sm = b < 0 ? 0 : b; t.pre_analysis = c ? 1 : 0;
+                t.link_mode = d ? 1 : 0; t.refill = r ? 1 : 0; t.ana_seq = q ? 1 : 0;
                 if (t.threads >= 64 && t.threads <= 512 && t.threads % 32 == 0) ctx->tune_table[cls] = t;
             }
             fclose(f);

@@ -314,3 +314,32 @@ def test_autotune_batched_keeps_labels_and_tunes_its_class():
         assert ccl.ccl_autotune_batched(c, 0, [0], [0], rp, ci, bits, out)[0] == ccl.CCL_OK
     finally:
         ccl.ccl_context_destroy(c)
+
+
+def test_tune_cache_file_roundtrip(tmp_path, monkeypatch):
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("CCL_TUNE_CACHE", str(path))
+    lat = L.triangle(512, 0.35, 3)
+    want = oracle.uf_label(lat)
+    rp, ci, bits = to_dev(lat)
+    out = torch.empty(lat.n, dtype=torch.int32, device=DEV)
+    c = ccl.ccl_context_create(0)
+    try:
+        st, best = ccl.ccl_autotune(c, lat.n, lat.nnz, rp, ci, bits, out)
+        assert st == ccl.CCL_OK and best > 0
+        assert np.array_equal(out.cpu().numpy(), want)
+    finally:
+        ccl.ccl_context_destroy(c)
+    rows = [list(map(int, l.split())) for l in path.read_text().splitlines() if l.strip()]
+    assert len(rows) >= 1 and all(len(r) == 7 for r in rows)
+    assert all(r[1] in (128, 256, 512) and r[3] in (0, 1) and r[4] in (0, 1) for r in rows)
+    # a new context reads the table back; malformed lines are skipped
+    path.write_text("not a line\n" + path.read_text() + "1 2 3\n")
+    c = ccl.ccl_context_create(0)
+    try:
+        out.fill_(-1)
+        assert ccl.ccl_label(c, lat.n, lat.nnz, rp, ci, bits, out) == ccl.CCL_OK
+        assert ccl.ccl_sync(c) == ccl.CCL_OK
+        assert np.array_equal(out.cpu().numpy(), want)
+    finally:
+        ccl.ccl_context_destroy(c)

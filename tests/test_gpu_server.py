@@ -102,3 +102,22 @@ def test_admission_waits_for_memory():
         srv.close()
     for lat, got in zip(reqs, outs):
         assert np.array_equal(got, oracle.uf_label(lat))
+
+
+def test_wait_timeout_keeps_the_ticket():
+    """A wait that times out leaves the ticket pending; a later wait returns
+    the labels."""
+    lat = L.triangle(1500, L.PC_TRIANGLE, 9)
+    srv = ccl.ccl_server_create(0, n_streams=1)
+    try:
+        t = _submit(srv, lat)
+        out = np.full(lat.n, -1, np.int32)
+        st = ccl.ccl_server_wait(srv, t, out, 0)
+        assert st in (ccl.CCL_OK, ccl.CCL_ERR_TIMEOUT)
+        if st == ccl.CCL_ERR_TIMEOUT:
+            assert np.array_equal(_wait(srv, t, lat.n), oracle.uf_label(lat))
+        else:
+            assert np.array_equal(out, oracle.uf_label(lat))
+            assert ccl.ccl_server_wait(srv, t, out, 0) == ccl.CCL_ERR_NOT_FOUND
+    finally:
+        ccl.ccl_server_destroy(srv)
