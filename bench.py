@@ -637,6 +637,16 @@ def run_served(args, rank, world, local):
     mean_sites = float(np.mean([lat.n for lat in req]))
     out_bufs = {id(lat): np.empty(lat.n, np.int32) for lat in pool}
 
+    def submit_nocopy(srv, lat):
+        # the pool's arrays stay alive and unchanged for the whole run
+        while True:
+            st, t = ccl.ccl_server_submit_nocopy(srv, lat.n, lat.nnz, lat.row_ptr, lat.col_idx, lat.open_bits)
+            if st == ccl.CCL_OK:
+                return t
+            if st != ccl.CCL_ERR_REJECTED:
+                raise ccl.CclError(st, "ccl_server_submit_nocopy")
+            time.sleep(0.0005)
+
     def submit(srv, lat):
         while True:
             st, t = ccl.ccl_server_submit(srv, lat.n, lat.nnz, lat.row_ptr, lat.col_idx, lat.open_bits)
@@ -654,38 +664,42 @@ def run_served(args, rank, world, local):
                 keep[k] = buf
 
     # closed loop: at most `window` requests in flight
-    srv = ccl.ccl_server_create(local, n_streams=args.streams, max_batch=1024, host_staging_bytes=4 << 30)
-    warm = [submit(srv, lat) for lat in pool[:16]]
-    drain(srv, warm, pool[:16])
     clocks = ClockSampler(local)
-    clocks.start()
-    done_at = [0.0] * len(req)
-    tickets = [None] * len(req)
-    sem = threading.Semaphore(args.window)
 
-    def feeder():
+    def closed_loop(nocopy: bool):
+        srv = ccl.ccl_server_create(local, n_streams=args.streams, max_batch=1024, host_staging_bytes=4 << 30)
+        sub = submit_nocopy if nocopy else submit
+        drain(srv, [sub(srv, lat) for lat in pool[:16]], pool[:16])
+        tickets = [None] * len(req)
+        sem = threading.Semaphore(args.window)
+
+        def feeder():
+            for k, lat in enumerate(req):
+                sem.acquire()
+                tickets[k] = sub(srv, lat)
+
+        keep = {k: None for k in range(0, len(req), max(1, len(req) // args.parity_sample))}
+        t0 = time.perf_counter()
+        th = threading.Thread(target=feeder)
+        th.start()
         for k, lat in enumerate(req):
-            sem.acquire()
-            tickets[k] = submit(srv, lat)
+            while tickets[k] is None:
+                time.sleep(0.00005)
+            buf = np.empty(lat.n, np.int32) if k in keep else out_bufs[id(lat)]
+            ccl.check(ccl.ccl_server_wait(srv, tickets[k], buf, 600_000), "ccl_server_wait")
+            if k in keep:
+                keep[k] = buf
+            sem.release()
+        th.join()
+        wall = time.perf_counter() - t0
+        st = ccl.ccl_server_stats_get(srv)
+        ccl.ccl_server_destroy(srv)
+        return wall, st, keep
 
-    keep = {k: None for k in range(0, len(req), max(1, len(req) // args.parity_sample))}
-    t0 = time.perf_counter()
-    th = threading.Thread(target=feeder)
-    th.start()
-    for k, lat in enumerate(req):
-        while tickets[k] is None:
-            time.sleep(0.00005)
-        buf = np.empty(lat.n, np.int32) if k in keep else out_bufs[id(lat)]
-        ccl.check(ccl.ccl_server_wait(srv, tickets[k], buf, 600_000), "ccl_server_wait")
-        if k in keep:
-            keep[k] = buf
-        done_at[k] = time.perf_counter()
-        sem.release()
-    th.join()
-    wall = time.perf_counter() - t0
+    clocks.start()
+    wall_copy, st_copy, keep_copy = closed_loop(False)
+    wall, st_closed, keep = closed_loop(True)
     clk = clocks.stop()
-    st_closed = ccl.ccl_server_stats_get(srv)
-    ccl.ccl_server_destroy(srv)
     total_sites = sum(lat.n for lat in req)
     capacity = total_sites / wall
 
@@ -696,7 +710,7 @@ def run_served(args, rank, world, local):
         rng = np.random.default_rng(55 + rank)
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(req)))
         srv = ccl.ccl_server_create(local, n_streams=args.streams, max_batch=1024, host_staging_bytes=4 << 30)
-        drain(srv, [submit(srv, lat) for lat in pool[:16]], pool[:16])
+        drain(srv, [submit_nocopy(srv, lat) for lat in pool[:16]], pool[:16])
         tk = [None] * len(req)
 
         def open_feeder():
@@ -705,7 +719,7 @@ def run_served(args, rank, world, local):
                 delay = base + arrivals[k] - time.perf_counter()
                 if delay > 0:
                     time.sleep(delay)
-                tk[k] = submit(srv, lat)
+                tk[k] = submit_nocopy(srv, lat)
 
         t1 = time.perf_counter()
         th = threading.Thread(target=open_feeder)
@@ -723,7 +737,7 @@ def run_served(args, rank, world, local):
                             "p50_ms": so.p50_ms, "p99_ms": so.p99_ms, "max_ms": so.max_ms,
                             "batches": int(so.batches)}
 
-    ok = all(np.array_equal(buf, oracle.uf_label(req[k])) for k, buf in keep.items())
+    ok = all(np.array_equal(buf, oracle.uf_label(req[k])) for kp in (keep, keep_copy) for k, buf in kp.items())
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
@@ -745,12 +759,16 @@ def run_served(args, rank, world, local):
             "config": {"workload": "served", "requests": len(req), "pool": len(pool),
                        "mean_sites": mean_sites, "window": args.window, "streams": args.streams,
                        "generation_s": t_gen, "l2": "inputs larger than L2 in aggregate (no flush)"},
-            "closed_loop": {"wall_s": wall, "requests_per_s": len(req) / wall, "batches": int(st_closed.batches),
+            "closed_loop": {"submit": "ccl_server_submit_nocopy", "wall_s": wall,
+                            "requests_per_s": len(req) / wall, "batches": int(st_closed.batches),
                             "p50_ms": st_closed.p50_ms, "p99_ms": st_closed.p99_ms},
+            "closed_loop_copying": {"submit": "ccl_server_submit", "sites_per_s": total_sites / wall_copy,
+                                    "requests_per_s": len(req) / wall_copy, "batches": int(st_copy.batches),
+                                    "p50_ms": st_copy.p50_ms, "p99_ms": st_copy.p99_ms},
             "open_loop": loads,
             "e2e": {"value": world * capacity, "unit": "sites/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": 4 * mean_sites,
-                    "entry": "ccl_server_submit / ccl_server_wait (host arrays in, labels out)"},
+                    "entry": "ccl_server_submit_nocopy / ccl_server_wait (host arrays in, labels out)"},
             "roofline": None,
             "cpu_baseline": cpu,
             "clocks": clk,

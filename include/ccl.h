@@ -366,6 +366,13 @@ CCL_API ccl_status ccl_server_create(ccl_server **srv, const ccl_server_config *
  * CCL_ERR_REJECTED if it can never fit the budget or the queue is full. */
 CCL_API ccl_status ccl_server_submit(ccl_server *srv, const ccl_request *req, uint64_t *ticket);
 
+/* As ccl_server_submit, without copying the request: the caller keeps
+ * req->row_ptr, col_idx and open_bits allocated and unchanged until
+ * ccl_server_wait has returned for the ticket (CCL_OK or an error other than
+ * CCL_ERR_TIMEOUT). The server uploads them from where they are (pinned or
+ * pageable host memory), which saves a host copy of the whole request. */
+CCL_API ccl_status ccl_server_submit_nocopy(ccl_server *srv, const ccl_request *req, uint64_t *ticket);
+
 /* Waits up to timeout_ms (< 0: forever) for the ticket, copies its labels to
  * labels_host (int32[n]) and forgets the ticket. */
 CCL_API ccl_status ccl_server_wait(ccl_server *srv, uint64_t ticket, int32_t *labels_host,

@@ -106,6 +106,7 @@ def _load() -> ctypes.CDLL:
         "ccl_autotune_batched": (C, [P, I32, P, P, P, P, P, P, P, ctypes.POINTER(ctypes.c_float)]),
         "ccl_server_create": (C, [ctypes.POINTER(P), ctypes.POINTER(ccl_server_config)]),
         "ccl_server_submit": (C, [P, ctypes.POINTER(ccl_request), ctypes.POINTER(ctypes.c_uint64)]),
+        "ccl_server_submit_nocopy": (C, [P, ctypes.POINTER(ccl_request), ctypes.POINTER(ctypes.c_uint64)]),
         "ccl_server_wait": (C, [P, ctypes.c_uint64, P, I64]),
         "ccl_server_stats_get": (C, [P, ctypes.POINTER(ccl_server_stats)]),
         "ccl_server_destroy": (None, [P]),
@@ -391,6 +392,17 @@ def ccl_server_submit(srv, n_sites: int, nnz: int, row_ptr, col_idx, open_bits):
                       _host_ptr(open_bits, "open_bits", np.uint32))
     t = ctypes.c_uint64(0)
     st = _lib.ccl_server_submit(srv, ctypes.byref(req), ctypes.byref(t))
+    return st, int(t.value)
+
+
+def ccl_server_submit_nocopy(srv, n_sites: int, nnz: int, row_ptr, col_idx, open_bits):
+    """Returns (status, ticket). The host arrays are NOT copied: keep them alive
+    and unchanged until ccl_server_wait has returned for the ticket."""
+    req = ccl_request(int(n_sites), 0, int(nnz), _host_ptr(row_ptr, "row_ptr", np.int32),
+                      _host_ptr(col_idx, "col_idx", np.int32),
+                      _host_ptr(open_bits, "open_bits", np.uint32))
+    t = ctypes.c_uint64(0)
+    st = _lib.ccl_server_submit_nocopy(srv, ctypes.byref(req), ctypes.byref(t))
     return st, int(t.value)
 
 

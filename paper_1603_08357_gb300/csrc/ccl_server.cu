@@ -1,15 +1,17 @@
 // Request loop of include/ccl.h: continuous batching of labelling requests.
 //
-// One server thread owns the GPU side. Each tick it
-//   1. admits pending requests while their device bytes fit the budget
-//      (the free HBM seen at start minus a reserve, and the configured
-//      cap), allocating their buffers from a stream-ordered pool and
-//      uploading them on an upload stream;
-//   2. gathers every request whose upload has finished into one batched
+// Two threads own the GPU side.
+//   The uploader admits pending requests while their device bytes fit the
+//   budget (the free HBM seen at start minus a reserve, and the configured
+//   cap), allocates their buffers from a stream-ordered pool and uploads
+//   them on an upload stream (copies from pageable memory block it while
+//   the driver stages them, so they are kept off the launch loop).
+//   The server thread, each tick,
+//   1. gathers every request whose upload has finished into one batched
 //      launch of the four labelling steps on a free compute stream (each
 //      compute stream has a labelling context of its own), followed by the
 //      copies of the labels back to host memory;
-//   3. retires finished batches: frees their buffers, stamps latencies and
+//   2. retires finished batches: frees their buffers, stamps latencies and
 //      wakes waiters.
 // Later requests are therefore uploaded and labelled while earlier batches
 // are still running. Every wait on the device is an event query; nothing
@@ -40,6 +42,7 @@ ccl_status label_instances(ccl_context *ctx, std::vector<Inst> &table, cudaStrea
 namespace {
 
 using Clock = std::chrono::steady_clock;
+constexpr int kUploaders = 2;    // uploader threads, each with a stream of its own
 
 struct Req {
     uint64_t ticket = 0;
@@ -49,6 +52,12 @@ struct Req {
     // (row_ptr | col_idx | bits | labels), else pageable vectors
     char *h = nullptr;
     size_t h_bytes = 0;
+    // no-copy requests: the caller's arrays, uploaded from where they are;
+    // only the labels come back through an arena block (lab_h) when it has room
+    const int32_t *ext_rp = nullptr, *ext_ci = nullptr;
+    const uint32_t *ext_bits = nullptr;
+    int32_t *lab_h = nullptr;
+    size_t lab_bytes = 0;
     std::vector<int32_t> v_row_ptr, v_col_idx, v_labels;
     std::vector<uint32_t> v_bits;
     int64_t dev_bytes = 0;
@@ -78,14 +87,24 @@ struct HostLayout {
     }
 };
 
-const int32_t *h_row_ptr(const Req &r) { return r.h ? (const int32_t *)(r.h) : r.v_row_ptr.data(); }
+const int32_t *h_row_ptr(const Req &r) {
+    if (r.ext_rp) return r.ext_rp;
+    return r.h ? (const int32_t *)(r.h) : r.v_row_ptr.data();
+}
 const int32_t *h_col_idx(const Req &r) {
+    if (r.ext_rp) return r.ext_ci;
     return r.h ? (const int32_t *)(r.h + HostLayout(r.n, r.nnz).ci) : r.v_col_idx.data();
 }
 const uint32_t *h_bits(const Req &r) {
+    if (r.ext_rp) return r.ext_bits;
     return r.h ? (const uint32_t *)(r.h + HostLayout(r.n, r.nnz).bits) : r.v_bits.data();
 }
-int32_t *h_labels(Req &r) { return r.h ? (int32_t *)(r.h + HostLayout(r.n, r.nnz).lab) : r.v_labels.data(); }
+int32_t *h_labels(Req &r) {
+    if (r.lab_h) return r.lab_h;
+    return r.h ? (int32_t *)(r.h + HostLayout(r.n, r.nnz).lab) : r.v_labels.data();
+}
+// labels come back by an asynchronous copy into pinned memory (else retire copies them)
+bool pinned_labels(const Req &r) { return r.h != nullptr || r.lab_h != nullptr; }
 
 // Host copies between caller memory and the pinned staging arena, split
 // across a few persistent threads: one thread moves about 10 GB/s, well
@@ -195,21 +214,24 @@ struct ccl_server {
     std::vector<ccl_context *> ctxs;
     std::vector<cudaStream_t> streams;
     std::vector<bool> slot_busy;
-    cudaStream_t upload = nullptr;
+    cudaStream_t upload = nullptr;                 // the first uploader's stream (teardown frees)
+    std::vector<cudaStream_t> upload_streams;     // one per uploader thread
     cudaMemPool_t pool = nullptr;
     char *h_stage = nullptr;
     HostArena arena;
     std::unique_ptr<CopyPool> copier;
 
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
+    std::condition_variable cv_work, cv_done, cv_upload;
     std::deque<std::shared_ptr<Req>> pending;
     std::map<uint64_t, std::shared_ptr<Req>> tickets;
     uint64_t next_ticket = 1;
     bool stop = false;
 
-    // owned by the server thread
+    // uploads in flight (uploader thread pushes, server thread pops; under mu)
     std::deque<std::shared_ptr<Req>> uploading;
+    int uploaders_running = 0;
+    // owned by the server thread
     std::vector<std::shared_ptr<Req>> ready;
     std::vector<Batch> inflight;
 
@@ -220,6 +242,7 @@ struct ccl_server {
     Clock::time_point t_first, t_last;
 
     std::thread th;
+    std::vector<std::thread> uploaders;
 };
 
 namespace {
@@ -227,7 +250,7 @@ namespace {
 void retire(ccl_server *S, Batch &b) {
     ccl_status st = ccl_sync(S->ctxs[(size_t)b.slot], S->streams[(size_t)b.slot], 0);
     for (auto &r : b.reqs) {
-        if (!r->h && r->n > 0) {   // pageable request: its labels come back now
+        if (!pinned_labels(*r) && r->n > 0) {   // pageable request: its labels come back now
             r->v_labels.resize((size_t)r->n);
             const size_t off = HostLayout(r->n, r->nnz).lab;
             if (cudaMemcpy(r->v_labels.data(), r->d_mem + off, (size_t)r->n * 4, cudaMemcpyDeviceToHost) !=
@@ -259,30 +282,31 @@ void retire(ccl_server *S, Batch &b) {
     S->t_last = now;
     S->batches++;
     S->cv_done.notify_all();
+    S->cv_upload.notify_one();       // device memory was freed
 }
 
-// uploads one admitted request; returns false if the pool is exhausted
-bool start_upload(ccl_server *S, const std::shared_ptr<Req> &r) {
+// uploads one admitted request on stream `up`; returns false if the pool is exhausted
+bool start_upload(ccl_server *S, const std::shared_ptr<Req> &r, cudaStream_t up) {
     const HostLayout lay(r->n, r->nnz);
     void *mem = nullptr;
-    if (cudaMallocFromPoolAsync(&mem, lay.total, S->pool, S->upload) != cudaSuccess) {
+    if (cudaMallocFromPoolAsync(&mem, lay.total, S->pool, up) != cudaSuccess) {
         (void)cudaGetLastError();
         return false;
     }
     r->d_mem = (char *)mem;
-    if (r->h) {   // one contiguous pinned block: one copy
-        cudaMemcpyAsync(r->d_mem, r->h, lay.lab, cudaMemcpyHostToDevice, S->upload);
+    if (r->h && !r->ext_rp) {   // one contiguous pinned block: one copy
+        cudaMemcpyAsync(r->d_mem, r->h, lay.lab, cudaMemcpyHostToDevice, up);
     } else {
-        cudaMemcpyAsync(r->d_mem, h_row_ptr(*r), (size_t)(r->n + 1) * 4, cudaMemcpyHostToDevice, S->upload);
+        cudaMemcpyAsync(r->d_mem, h_row_ptr(*r), (size_t)(r->n + 1) * 4, cudaMemcpyHostToDevice, up);
         if (r->nnz > 0) {
             cudaMemcpyAsync(r->d_mem + lay.ci, h_col_idx(*r), (size_t)r->nnz * 4, cudaMemcpyHostToDevice,
-                            S->upload);
+                            up);
             cudaMemcpyAsync(r->d_mem + lay.bits, h_bits(*r), (size_t)((r->nnz + 31) / 32) * 4,
-                            cudaMemcpyHostToDevice, S->upload);
+                            cudaMemcpyHostToDevice, up);
         }
     }
     cudaEventCreateWithFlags(&r->uploaded, cudaEventDisableTiming);
-    cudaEventRecord(r->uploaded, S->upload);
+    cudaEventRecord(r->uploaded, up);
     return true;
 }
 
@@ -312,7 +336,7 @@ void launch_batch(ccl_server *S, int slot, std::vector<std::shared_ptr<Req>> req
     ccl_status st = ccl::label_instances(S->ctxs[(size_t)slot], table, s);
     for (size_t t = 0; t < reqs.size(); ++t) {
         auto &r = reqs[t];
-        if (r->h && r->n > 0)
+        if (pinned_labels(*r) && r->n > 0)
             cudaMemcpyAsync(h_labels(*r), table[t].labels, (size_t)r->n * 4, cudaMemcpyDeviceToHost, s);
         if (st != CCL_OK) r->status = st;
     }
@@ -329,36 +353,19 @@ void server_loop(ccl_server *S) {
     cudaSetDevice(S->cfg.device);
     for (;;) {
         bool progressed = false;
-        // 1. admission
+        // 1. collect uploaded requests (admission and uploads run on the uploader thread)
         {
-            std::unique_lock<std::mutex> lk(S->mu);
+            std::lock_guard<std::mutex> lk(S->mu);
             if (S->stop) break;
-            while (!S->pending.empty()) {
-                auto r = S->pending.front();
-                if (S->held + r->dev_bytes > S->budget && S->held > 0) break;
-                S->pending.pop_front();
-                S->held += r->dev_bytes;
-                lk.unlock();
-                const bool ok = start_upload(S, r);
-                lk.lock();
-                if (!ok) {     // pool full right now: retry later
-                    S->held -= r->dev_bytes;
-                    S->pending.push_front(r);
-                    break;
-                }
-                S->uploading.push_back(r);
+            while (!S->uploading.empty()) {
+                auto &r = S->uploading.front();
+                const cudaError_t e = cudaEventQuery(r->uploaded);
+                if (e == cudaErrorNotReady) break;
+                if (e != cudaSuccess) { (void)cudaGetLastError(); r->status = CCL_ERR_CUDA; }
+                S->ready.push_back(r);
+                S->uploading.pop_front();
                 progressed = true;
             }
-        }
-        // 2. collect uploaded requests
-        while (!S->uploading.empty()) {
-            auto &r = S->uploading.front();
-            const cudaError_t e = cudaEventQuery(r->uploaded);
-            if (e == cudaErrorNotReady) break;
-            if (e != cudaSuccess) { (void)cudaGetLastError(); r->status = CCL_ERR_CUDA; }
-            S->ready.push_back(r);
-            S->uploading.pop_front();
-            progressed = true;
         }
         // 3. launch on a free compute stream
         if (!S->ready.empty()) {
@@ -388,7 +395,12 @@ void server_loop(ccl_server *S) {
             S->cv_work.wait_for(lk, idle ? std::chrono::milliseconds(5) : std::chrono::microseconds(50));
         }
     }
-    // drain what is on the device before tearing down
+    // drain what is on the device before tearing down (after the uploader has stopped)
+    {
+        std::unique_lock<std::mutex> lk(S->mu);
+        S->cv_upload.notify_all();
+        S->cv_done.wait(lk, [&] { return S->uploaders_running == 0; });
+    }
     for (auto &b : S->inflight) {
         cudaEventSynchronize(b.finished);
         retire(S, b);
@@ -403,7 +415,42 @@ void server_loop(ccl_server *S) {
         if (r->d_mem) cudaFreeAsync(r->d_mem, S->upload);
         if (r->uploaded) cudaEventDestroy(r->uploaded);
     }
-    cudaStreamSynchronize(S->upload);
+    for (auto us : S->upload_streams) cudaStreamSynchronize(us);
+}
+
+// Admits pending requests while their device bytes fit the budget and uploads
+// them on the upload stream. Copies from pageable memory block the calling
+// thread while the driver stages them, so they run here, apart from the
+// launch/retire loop.
+void upload_loop(ccl_server *S, cudaStream_t up) {
+    cudaSetDevice(S->cfg.device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (!S->stop) {
+        if (S->pending.empty()) {
+            S->cv_upload.wait_for(lk, std::chrono::milliseconds(5));
+            continue;
+        }
+        auto r = S->pending.front();
+        if (S->held + r->dev_bytes > S->budget && S->held > 0) {   // wait for memory to free up
+            S->cv_upload.wait_for(lk, std::chrono::microseconds(200));
+            continue;
+        }
+        S->pending.pop_front();
+        S->held += r->dev_bytes;
+        lk.unlock();
+        const bool ok = start_upload(S, r, up);
+        lk.lock();
+        if (!ok) {     // pool full right now: retry later
+            S->held -= r->dev_bytes;
+            S->pending.push_front(r);
+            S->cv_upload.wait_for(lk, std::chrono::microseconds(200));
+            continue;
+        }
+        S->uploading.push_back(r);
+        S->cv_work.notify_one();
+    }
+    S->uploaders_running--;
+    S->cv_done.notify_all();
 }
 
 }  // namespace
@@ -449,7 +496,12 @@ ccl_status ccl_server_create(ccl_server **out, const ccl_server_config *cfg_in) 
         uint64_t thr = UINT64_MAX;   // keep freed memory in the pool
         cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->upload, cudaStreamNonBlocking);
+    for (int u = 0; u < kUploaders && e == cudaSuccess; ++u) {
+        cudaStream_t us = nullptr;
+        e = cudaStreamCreateWithFlags(&us, cudaStreamNonBlocking);
+        if (e == cudaSuccess) S->upload_streams.push_back(us);
+    }
+    if (e == cudaSuccess) S->upload = S->upload_streams[0];
     if (e == cudaSuccess && cfg.host_staging_bytes > 0) {
         e = cudaMallocHost(&S->h_stage, (size_t)cfg.host_staging_bytes);
         if (e == cudaSuccess) S->arena.init(S->h_stage, (size_t)cfg.host_staging_bytes);
@@ -468,7 +520,7 @@ ccl_status ccl_server_create(ccl_server **out, const ccl_server_config *cfg_in) 
         (void)cudaGetLastError();
         for (auto c : S->ctxs) ccl_context_destroy(c);
         for (auto s : S->streams) cudaStreamDestroy(s);
-        if (S->upload) cudaStreamDestroy(S->upload);
+        for (auto us : S->upload_streams) cudaStreamDestroy(us);
         if (S->pool) cudaMemPoolDestroy(S->pool);
         if (S->h_stage) cudaFreeHost(S->h_stage);
         delete S;
@@ -482,12 +534,17 @@ ccl_status ccl_server_create(ccl_server **out, const ccl_server_config *cfg_in) 
         if (const char *env = getenv("CCL_SERVER_COPY_THREADS")) nt = std::max(0, std::min(64, atoi(env)));
         S->copier.reset(new CopyPool(nt));
     }
+    S->uploaders_running = (int)S->upload_streams.size();
     S->th = std::thread(server_loop, S);
+    for (auto us : S->upload_streams) S->uploaders.emplace_back(upload_loop, S, us);
     *out = S;
     return CCL_OK;
 }
 
-ccl_status ccl_server_submit(ccl_server *S, const ccl_request *req, uint64_t *ticket) {
+}  // extern "C"
+
+namespace {
+ccl_status server_submit(ccl_server *S, const ccl_request *req, uint64_t *ticket, bool copy) {
     if (!S || !req || !ticket) return CCL_ERR_INVALID_ARGUMENT;
     if (req->n_sites < 0 || req->nnz < 0 || req->nnz > INT32_MAX) return CCL_ERR_INVALID_ARGUMENT;
     if (!req->row_ptr || (req->nnz > 0 && (!req->col_idx || !req->open_bits)))
@@ -507,22 +564,31 @@ ccl_status ccl_server_submit(ccl_server *S, const ccl_request *req, uint64_t *ti
         }
     }
     r->t_submit = Clock::now();
-    {
+    if (!copy) {
+        r->ext_rp = req->row_ptr;
+        r->ext_ci = req->nnz > 0 ? req->col_idx : req->row_ptr;
+        r->ext_bits = req->nnz > 0 ? req->open_bits : (const uint32_t *)req->row_ptr;
         std::lock_guard<std::mutex> lk(S->mu);
-        r->h = S->arena.alloc(lay.total);
-        if (r->h) r->h_bytes = lay.total;
-    }
-    if (r->h) {
-        S->copier->copy(r->h, req->row_ptr, (size_t)(r->n + 1) * 4);
-        if (r->nnz > 0) {
-            S->copier->copy(r->h + lay.ci, req->col_idx, (size_t)r->nnz * 4);
-            S->copier->copy(r->h + lay.bits, req->open_bits, (size_t)((r->nnz + 31) / 32) * 4);
-        }
+        r->lab_h = (int32_t *)S->arena.alloc((size_t)r->n * 4 + 4);
+        if (r->lab_h) r->lab_bytes = (size_t)r->n * 4 + 4;
     } else {
-        r->v_row_ptr.assign(req->row_ptr, req->row_ptr + r->n + 1);
-        r->v_col_idx.assign(req->col_idx, req->col_idx + r->nnz);
-        r->v_bits.assign(req->open_bits, req->open_bits + (r->nnz + 31) / 32);
-        if (r->v_bits.empty()) r->v_bits.push_back(0);
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            r->h = S->arena.alloc(lay.total);
+            if (r->h) r->h_bytes = lay.total;
+        }
+        if (r->h) {
+            S->copier->copy(r->h, req->row_ptr, (size_t)(r->n + 1) * 4);
+            if (r->nnz > 0) {
+                S->copier->copy(r->h + lay.ci, req->col_idx, (size_t)r->nnz * 4);
+                S->copier->copy(r->h + lay.bits, req->open_bits, (size_t)((r->nnz + 31) / 32) * 4);
+            }
+        } else {
+            r->v_row_ptr.assign(req->row_ptr, req->row_ptr + r->n + 1);
+            r->v_col_idx.assign(req->col_idx, req->col_idx + r->nnz);
+            r->v_bits.assign(req->open_bits, req->open_bits + (r->nnz + 31) / 32);
+            if (r->v_bits.empty()) r->v_bits.push_back(0);
+        }
     }
     {
         std::lock_guard<std::mutex> lk(S->mu);
@@ -533,8 +599,19 @@ ccl_status ccl_server_submit(ccl_server *S, const ccl_request *req, uint64_t *ti
         if (!S->have_first) { S->have_first = true; S->t_first = r->t_submit; }
         *ticket = r->ticket;
     }
-    S->cv_work.notify_one();
+    S->cv_upload.notify_one();
     return CCL_OK;
+}
+}  // namespace
+
+extern "C" {
+
+ccl_status ccl_server_submit(ccl_server *S, const ccl_request *req, uint64_t *ticket) {
+    return server_submit(S, req, ticket, true);
+}
+
+ccl_status ccl_server_submit_nocopy(ccl_server *S, const ccl_request *req, uint64_t *ticket) {
+    return server_submit(S, req, ticket, false);
 }
 
 ccl_status ccl_server_wait(ccl_server *S, uint64_t ticket, int32_t *labels_host, int64_t timeout_ms) {
@@ -556,6 +633,7 @@ ccl_status ccl_server_wait(ccl_server *S, uint64_t ticket, int32_t *labels_host,
         S->tickets.erase(ticket);
     }
     if (r->h) { S->arena.release(r->h, r->h_bytes); r->h = nullptr; }
+    if (r->lab_h) { S->arena.release((char *)r->lab_h, r->lab_bytes); r->lab_h = nullptr; }
     r->v_labels.clear();
     r->v_labels.shrink_to_fit();
     return r->status;
@@ -592,12 +670,15 @@ void ccl_server_destroy(ccl_server *S) {
         S->stop = true;
     }
     S->cv_work.notify_all();
+    S->cv_upload.notify_all();
+    for (auto &u : S->uploaders)
+        if (u.joinable()) u.join();
     if (S->th.joinable()) S->th.join();
     S->copier.reset();
     cudaSetDevice(S->cfg.device);
     for (auto c : S->ctxs) ccl_context_destroy(c);
     for (auto s : S->streams) cudaStreamDestroy(s);
-    if (S->upload) cudaStreamDestroy(S->upload);
+    for (auto us : S->upload_streams) cudaStreamDestroy(us);
     if (S->pool) cudaMemPoolDestroy(S->pool);
     if (S->h_stage) cudaFreeHost(S->h_stage);
     (void)cudaGetLastError();

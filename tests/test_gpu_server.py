@@ -121,3 +121,23 @@ def test_wait_timeout_keeps_the_ticket():
             assert ccl.ccl_server_wait(srv, t, out, 0) == ccl.CCL_ERR_NOT_FOUND
     finally:
         ccl.ccl_server_destroy(srv)
+
+
+def test_nocopy_requests_match_oracle():
+    """Requests submitted without a copy (arrays kept alive by the caller),
+    mixed with copied ones, give the oracle's labels."""
+    reqs = _requests(120, 13)
+    srv = ccl.ccl_server_create(0, n_streams=2, max_batch=32)
+    try:
+        tickets = []
+        for k, lat in enumerate(reqs):
+            if k % 2:
+                st, t = ccl.ccl_server_submit_nocopy(srv, lat.n, lat.nnz, lat.row_ptr, lat.col_idx, lat.open_bits)
+                assert st == ccl.CCL_OK, ccl.ccl_status_string(st)
+            else:
+                t = _submit(srv, lat)
+            tickets.append(t)
+        for t, lat in zip(tickets, reqs):
+            assert np.array_equal(_wait(srv, t, lat.n), oracle.uf_label(lat))
+    finally:
+        ccl.ccl_server_destroy(srv)
