@@ -349,6 +349,77 @@ __device__ __forceinline__ void init_scan_chunk(const Params &P, const Stage &S,
     cr.r = cnt > 1 ? cnt - 1 : 0;
 }
 
+// Both chunks of a consumer warp at once, when every row of both is short and
+// staged (the common case): the two rows of a lane are scanned in one loop,
+// so their shared-memory loads and dependent arithmetic interleave. Returns
+// false (having done nothing) otherwise.
+template <bool kBatched, bool kGen = false>
+__device__ __forceinline__ bool init_scan_pair(const Params &P, const Stage &S, const Inst &I, int cc0,
+                                               int lane, const TileCtx &tc, ChunkRes &c0, ChunkRes &c1) {
+    const StageHdr &h = S.h;
+    const int32_t n = I.n;
+    const int32_t s00 = h.s0 + cc0 * kChunk;
+    if (!tc.staged || s00 + 2 * kChunk > n || s00 < h.rp_lo || s00 + 2 * kChunk >= h.rp_hi) return false;
+    const int32_t i0 = s00 + lane, i1 = i0 + kChunk;
+    const int32_t *rp = S.rp + (s00 - h.rp_lo);
+    int32_t a0 = rp[lane], b0 = rp[lane + 1], a1 = rp[lane + kChunk], b1 = rp[lane + kChunk + 1];
+    const bool ok0 = a0 >= h.e0 && a0 <= b0 && b0 <= h.e1, ok1 = a1 >= h.e0 && a1 <= b1 && b1 <= h.e1;
+    const int32_t d0 = b0 - a0, d1 = b1 - a1;
+    const int32_t dmax = __reduce_max_sync(kFull, (uint32_t)max(ok0 ? d0 : 0, ok1 ? d1 : 0));
+    if (!__all_sync(kFull, ok0 && ok1) || dmax > kRowRegs) return false;
+    const int32_t *col0 = S.ci + (a0 - h.ci_lo), *col1 = S.ci + (a1 - h.ci_lo);
+    uint32_t w0 = 0, w1 = 0;
+    if (!kGen) {
+        const int32_t r0 = tc.rb0 + a0, r1 = tc.rb0 + a1;
+        if (d0 > 0) w0 = __funnelshift_r(S.bw[r0 >> 5], S.bw[(r0 + d0 - 1) >> 5], (uint32_t)r0 & 31u);
+        if (d1 > 0) w1 = __funnelshift_r(S.bw[r1 >> 5], S.bw[(r1 + d1 - 1) >> 5], (uint32_t)r1 & 31u);
+    }
+    int32_t m0 = INT32_MAX, m1 = INT32_MAX, k0 = -1, k1 = -1;
+    uint32_t l0 = 0, l1 = 0, jmax = 0;
+#pragma unroll
+    for (int t = 0; t < kRowRegs; ++t) {
+        if (t >= dmax) break;
+        if (t < d0) {
+            const int32_t j = col0[t];
+            jmax = max(jmax, (uint32_t)j);
+            const bool open = kGen ? ((uint32_t)j < (uint32_t)i0 &&
+                                      gen_bond_open(P.gen_seed, P.gen_thr, (uint32_t)j, (uint32_t)i0))
+                                   : ((w0 >> t) & 1u) != 0;
+            if (open && (uint32_t)j < (uint32_t)i0) {
+                l0 |= 1u << t;
+                if (j < m0) { m0 = j; k0 = t; }
+            }
+        }
+        if (t < d1) {
+            const int32_t j = col1[t];
+            jmax = max(jmax, (uint32_t)j);
+            const bool open = kGen ? ((uint32_t)j < (uint32_t)i1 &&
+                                      gen_bond_open(P.gen_seed, P.gen_thr, (uint32_t)j, (uint32_t)i1))
+                                   : ((w1 >> t) & 1u) != 0;
+            if (open && (uint32_t)j < (uint32_t)i1) {
+                l1 |= 1u << t;
+                if (j < m1) { m1 = j; k1 = t; }
+            }
+        }
+    }
+    if (jmax >= (uint32_t)n) raise_err(P.err, kErrIndex);
+    const int n0 = __popc(l0), n1 = __popc(l1);
+    int32_t lab0 = n0 ? m0 : i0, lab1 = n1 ? m1 : i1;
+    if (n0) {
+        const int32_t mt = (int32_t)((uint32_t)m0 / kTileSites);
+        if (mt >= tc.vis_lo && mt <= tc.vis_hi) lab0 = __ldcg(I.labels + m0);
+    }
+    if (n1) {
+        const int32_t mt = (int32_t)((uint32_t)m1 / kTileSites);
+        if (mt >= tc.vis_lo && mt <= tc.vis_hi) lab1 = __ldcg(I.labels + m1);
+    }
+    c0.i = i0; c0.a = a0; c0.a_next = b0; c0.mk = k0; c0.lab = lab0; c0.fast = true;
+    c0.resmask = n0 ? (l0 & ~(1u << k0)) : 0u; c0.r = n0 > 1 ? n0 - 1 : 0;
+    c1.i = i1; c1.a = a1; c1.a_next = b1; c1.mk = k1; c1.lab = lab1; c1.fast = true;
+    c1.resmask = n1 ? (l1 & ~(1u << k1)) : 0u; c1.r = n1 > 1 ? n1 - 1 : 0;
+    return true;
+}
+
 // Writes the residual pairs of one scanned chunk from queue slot `slot` on.
 // A pair {i, j} is stored as (label[i], j): label[i] is i's parent in the
 // label forest and, i not being a root, step (iii) never rewrites it, so the
@@ -440,8 +511,10 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
             ChunkRes c0, c1;
             c0.r = c1.r = 0;
             const bool has0 = cc0 * kChunk < S.h.ts, has1 = cc1 * kChunk < S.h.ts;
-            if (has0) init_scan_chunk<kBatched, kGen>(P, S, I, cc0, lane, tc, c0);
-            if (has1) init_scan_chunk<kBatched, kGen>(P, S, I, cc1, lane, tc, c1);
+            if (!(has1 && init_scan_pair<kBatched, kGen>(P, S, I, cc0, lane, tc, c0, c1))) {
+                if (has0) init_scan_chunk<kBatched, kGen>(P, S, I, cc0, lane, tc, c0);
+                if (has1) init_scan_chunk<kBatched, kGen>(P, S, I, cc1, lane, tc, c1);
+            }
             if (has0 && c0.i < I.n) I.labels[c0.i] = c0.lab;
             if (has1 && c1.i < I.n) I.labels[c1.i] = c1.lab;
             const int rr = c0.r + c1.r;
