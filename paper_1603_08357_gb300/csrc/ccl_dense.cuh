@@ -357,6 +357,63 @@ __device__ __forceinline__ void dense_scan_chunk(const Params &P, const DenseSta
     c.r = cnt > 1 ? cnt - 1 : 0;
 }
 
+// Both chunks of a consumer warp at once on a staged tile whose two chunks
+// are full: each slot's header offsets are read once and the two chunks'
+// loads interleave. Returns false (having done nothing) otherwise.
+template <bool kGen>
+__device__ __forceinline__ bool dense_scan_pair(const Params &P, const DenseStage &S, int cc0, int lane,
+                                                const TileCtx &tc, DenseChunk &c0, DenseChunk &c1) {
+    const DenseStageHdr &h = S.h;
+    const int64_t n = P.one.n;
+    const int W = (int)P.nn_width;
+    const int32_t loc0 = cc0 * kChunk + lane, loc1 = loc0 + kChunk;
+    if (!tc.staged || (cc0 + 2) * kChunk > h.ts) return false;
+    const int32_t i0 = h.s0 + loc0, i1 = i0 + kChunk;
+    int32_t m0 = INT32_MAX, m1 = INT32_MAX, k0 = 0, k1 = 0;
+    uint32_t l0 = 0, l1 = 0;
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < kRowRegs; ++k) {
+        if (k >= W) break;
+        const int2 off = h.off[k];
+        const int32_t j0 = S.nn[k][off.x + loc0], j1 = S.nn[k][off.x + loc1];
+        bool o0, o1;
+        if (kGen) {
+            o0 = (uint32_t)j0 < (uint32_t)i0 && gen_bond_open(P.gen_seed, P.gen_thr, (uint32_t)j0, (uint32_t)i0);
+            o1 = (uint32_t)j1 < (uint32_t)i1 && gen_bond_open(P.gen_seed, P.gen_thr, (uint32_t)j1, (uint32_t)i1);
+        } else {
+            const int32_t b0 = off.y + loc0, b1 = b0 + kChunk;
+            o0 = (S.bw[k][b0 >> 5] >> (b0 & 31)) & 1u;
+            o1 = (S.bw[k][b1 >> 5] >> (b1 & 31)) & 1u;
+        }
+        bad |= (uint32_t)(j0 + 1) > (uint32_t)n || (uint32_t)(j1 + 1) > (uint32_t)n;
+        if (o0 && (uint32_t)j0 < (uint32_t)i0) {
+            l0 |= 1u << k;
+            if (j0 < m0) { m0 = j0; k0 = k; }
+        }
+        if (o1 && (uint32_t)j1 < (uint32_t)i1) {
+            l1 |= 1u << k;
+            if (j1 < m1) { m1 = j1; k1 = k; }
+        }
+    }
+    if (bad) raise_err(P.err, kErrIndex);
+    const int n0 = __popc(l0), n1 = __popc(l1);
+    int32_t lab0 = n0 ? m0 : i0, lab1 = n1 ? m1 : i1;
+    if (n0) {
+        const int32_t mt = (int32_t)((uint32_t)m0 / kTileSites);
+        if (mt >= tc.vis_lo && mt <= tc.vis_hi) lab0 = __ldcg(P.one.labels + m0);
+    }
+    if (n1) {
+        const int32_t mt = (int32_t)((uint32_t)m1 / kTileSites);
+        if (mt >= tc.vis_lo && mt <= tc.vis_hi) lab1 = __ldcg(P.one.labels + m1);
+    }
+    c0.i = i0; c0.lab = lab0; c0.m = m0; c0.mk = k0;
+    c0.lowmask = n0 ? (l0 & ~(1u << k0)) : 0u; c0.r = n0 > 1 ? n0 - 1 : 0;
+    c1.i = i1; c1.lab = lab1; c1.m = m1; c1.mk = k1;
+    c1.lowmask = n1 ? (l1 & ~(1u << k1)) : 0u; c1.r = n1 > 1 ? n1 - 1 : 0;
+    return true;
+}
+
 template <bool kGen>
 __device__ __forceinline__ void dense_emit_chunk(const Params &P, const DenseStage &S, const DenseChunk &c,
                                                  bool staged, int64_t slot) {
@@ -423,8 +480,10 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init_dense_tma(Params P) {
         DenseChunk c0, c1;
         c0.r = c1.r = 0;
         const bool has0 = cc0 * kChunk < S.h.ts, has1 = cc1 * kChunk < S.h.ts;
-        if (has0) dense_scan_chunk<kGen>(P, S, cc0, lane, tc, c0);
-        if (has1) dense_scan_chunk<kGen>(P, S, cc1, lane, tc, c1);
+        if (!(has1 && dense_scan_pair<kGen>(P, S, cc0, lane, tc, c0, c1))) {
+            if (has0) dense_scan_chunk<kGen>(P, S, cc0, lane, tc, c0);
+            if (has1) dense_scan_chunk<kGen>(P, S, cc1, lane, tc, c1);
+        }
         if (has0 && c0.i < P.one.n) P.one.labels[c0.i] = c0.lab;
         if (has1 && c1.i < P.one.n) P.one.labels[c1.i] = c1.lab;
         const int rr = c0.r + c1.r;
