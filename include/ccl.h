@@ -73,7 +73,7 @@ CCL_API const char *ccl_status_string(int status);
 CCL_API int ccl_version(void);
 
 /* Creates a context on CUDA device `device`: it owns the workspace (residual
- * pair queue, per-chunk records), the error word, the tuning table and the
+ * pair queue, band records), the error word, the tuning table and the
  * captured CUDA graphs. Not thread-safe: one host thread per context. */
 CCL_API ccl_status ccl_context_create(ccl_context **ctx, int device);
 CCL_API void ccl_context_destroy(ccl_context *ctx);
@@ -216,8 +216,10 @@ CCL_API ccl_status ccl_label_noalloc(int32_t n_sites, int64_t nnz, const int32_t
                                      const int32_t *col_idx, const uint32_t *open_bits,
                                      int32_t *labels, void *stream);
 
-/* Pre-sizes the workspace for instances of up to n sites and nnz entries in
- * total (and up to n_chunks 32-site chunks; 0 = ceil(n/32)). */
+/* Pre-sizes the workspace for calls of up to nnz CSR entries in total (one
+ * queue slot each), so later calls up to that size allocate nothing (e.g.
+ * before capturing a stream into a graph). n_sites and n_chunks are checked
+ * for sign only (the workspace does not depend on them). */
 CCL_API ccl_status ccl_reserve(ccl_context *ctx, int64_t n_sites, int64_t nnz, int64_t n_chunks);
 
 /*

@@ -7,13 +7,18 @@
 //  * Step (i) streams the CSR input: per CTA one producer warp moves each
 //    tile's row pointers, column indices and bit words into shared memory with
 //    bulk asynchronous copies (cp.async.bulk, completion on mbarriers, a ring
-//    of kStages stages); eight consumer warps scan the rows and write the
-//    labels, the chunk records and the residual pairs. A chunk's pairs go to
-//    queue slots fixed by its first CSR entry, so no global counter is needed.
-//  * Steps (ii)/(iv) and (iii) chase label chains. Chains have a long tail,
-//    so instead of one chain per lane per round a lane that finishes takes
-//    the next site (pair) of its warp's window: the warp's loads stay busy
-//    until the window is drained.
+//    of kStages stages); kInitConsumers consumer warps scan the rows (two
+//    chunks per warp and tile, interleaved), write the labels and append the
+//    residual pairs to their CTA's part of the queue through one prefix sum
+//    per warp and tile. Each CTA owns a contiguous band of tiles; a site whose
+//    smallest lower neighbour lies in a band tile finished kStages tiles
+//    earlier takes that neighbour's label (most of step (ii) on lattices).
+//  * Step (iii) runs Algorithm 1 over the queue: each warp drains a window of
+//    pairs with four pairs per lane in lockstep rounds (one load or atomicMin
+//    per live pair per round, next state by selects).
+//  * Steps (ii)/(iv) chase every site's chain to its root, two chains per
+//    lane at once, each warp over a contiguous range of sites (or
+//    interleaved, for inputs without locality).
 #pragma once
 #include <stdint.h>
 #include <cuda_runtime.h>
