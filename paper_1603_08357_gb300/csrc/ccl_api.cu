@@ -494,13 +494,16 @@ Params base_params(ccl_context *ctx, const TuneChoice &tc) {
     return P;
 }
 
+// Argument checks of the single-instance calls; need_bits is false for the
+// calls that draw the bonds on the device.
 ccl_status check_single_args(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
-                             const int32_t *col_idx, const uint32_t *bits, const int32_t *labels) {
+                             const int32_t *col_idx, const uint32_t *bits, const int32_t *labels,
+                             bool need_bits = true) {
     if (!ctx) return CCL_ERR_INVALID_ARGUMENT;
     if (n < 0 || nnz < 0 || nnz > INT32_MAX) return CCL_ERR_INVALID_ARGUMENT;
     if (n == 0) return CCL_OK;
     if (!row_ptr || !labels) return CCL_ERR_INVALID_ARGUMENT;
-    if (nnz > 0 && (!col_idx || !bits)) return CCL_ERR_INVALID_ARGUMENT;
+    if (nnz > 0 && (!col_idx || (need_bits && !bits))) return CCL_ERR_INVALID_ARGUMENT;
     return CCL_OK;
 }
 
@@ -875,7 +878,7 @@ ccl_status ccl_autotune_batched(ccl_context *ctx, int32_t K, const int64_t *site
 ccl_status ccl_label_random(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
                             const int32_t *col_idx, uint64_t seed, double p, int32_t *labels,
                             void *stream) {
-    ccl_status st = check_single_args(ctx, n, nnz, row_ptr, col_idx, (const uint32_t *)1, labels);
+    ccl_status st = check_single_args(ctx, n, nnz, row_ptr, col_idx, nullptr, labels, false);
     if (st != CCL_OK || n == 0) return st;
     if (!(p >= 0.0 && p <= 1.0)) return CCL_ERR_INVALID_ARGUMENT;
     // open iff (output >> 11) * 2^-53 < p  <=>  (output >> 11) < ceil(p * 2^53)
@@ -887,10 +890,10 @@ ccl_status ccl_label_random(ccl_context *ctx, int32_t n, int64_t nnz, const int3
 
 namespace {
 ccl_status check_dense_args(ccl_context *ctx, int32_t n, int32_t width, const int32_t *nn, const void *bits,
-                            const int32_t *labels) {
+                            const int32_t *labels, bool need_bits = true) {
     if (!ctx || n < 0 || width < 0 || width > CCL_DENSE_MAX_WIDTH) return CCL_ERR_INVALID_ARGUMENT;
     if (n == 0) return CCL_OK;
-    if (!labels || (width > 0 && (!nn || !bits))) return CCL_ERR_INVALID_ARGUMENT;
+    if (!labels || (width > 0 && (!nn || (need_bits && !bits)))) return CCL_ERR_INVALID_ARGUMENT;
     return CCL_OK;
 }
 }  // namespace
@@ -907,7 +910,7 @@ ccl_status ccl_label_dense(ccl_context *ctx, int32_t n, int32_t width, const int
 
 ccl_status ccl_label_dense_random(ccl_context *ctx, int32_t n, int32_t width, const int32_t *nn,
                                   uint64_t seed, double p, int32_t *labels, void *stream) {
-    ccl_status st = check_dense_args(ctx, n, width, nn, (const void *)1, labels);
+    ccl_status st = check_dense_args(ctx, n, width, nn, nullptr, labels, false);
     if (st != CCL_OK || n == 0) return st;
     if (!(p >= 0.0 && p <= 1.0)) return CCL_ERR_INVALID_ARGUMENT;
     DeviceGuard guard(ctx->device);
