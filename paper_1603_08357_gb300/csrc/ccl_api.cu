@@ -71,9 +71,12 @@ struct ccl_context {
     Inst *h_insts = nullptr;     // pinned staging
     int64_t h_insts_cap = 0;
     cudaEvent_t staging_free = nullptr;
-    // host-buffer path
+    // host-buffer path: device copies of the inputs, and the copy stream and
+    // events that overlap the upload of later parts with step (i) on earlier ones
     void *d_host_in = nullptr;
     int64_t host_in_cap = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t part_ev[5] = {};
     // relabel / spanning scratch
     void *d_aux = nullptr;
     int64_t aux_cap = 0;
@@ -266,38 +269,46 @@ TuneChoice choice_for(ccl_context *ctx, int64_t n, int64_t nnz) {
     return ctx->opt;
 }
 
-// Enqueues the four steps. All kernels read their sizes from Params, so the
-// sequence contains no host synchronisation and can be captured.
-ccl_status enqueue_steps(ccl_context *ctx, const Params &P0, bool batched, const TuneChoice &tc,
-                         cudaStream_t s, bool profile) {
-    const int T = tc.threads;
-    const int64_t warps_chunks = (P0.n_chunks + kAnaChunks - 1) / kAnaChunks;
-    Params P = P0;
-    const bool dense = P.dense != 0;
+// Grid of step (i) over P.n_tiles tiles: CTAs (bands) of the kernel variant P
+// selects, at most max_bands.
+int64_t init_grid(ccl_context *ctx, const Params &P, bool batched, int64_t max_bands) {
     const bool gen = P.gen_thr != kNoGen;
-    const bool dense_tma = dense && P.nn_width <= kRowRegs;
-    const int64_t g_init = dense_tma ? grid_init(ctx, gen ? 10 : 9, kInitThreads, P.n_tiles)
-                           : dense ? grid_init(ctx, gen ? 8 : 7, kDenseThreads, P.n_tiles)
-                                   : grid_init(ctx, batched ? 1 : (gen ? 6 : 0), kInitThreads, P.n_tiles);
-    P.n_bands = (int32_t)g_init;
-    const int64_t g_red = (int64_t)ctx->num_sms * blocks_per_sm(ctx, batched ? 5 : 4, 256);
-    CCL_CUDA(cudaMemsetAsync(P.counters, 0, 4 * sizeof(unsigned long long), s));
-    CCL_CUDA(cudaMemsetAsync(P.band, 0, (size_t)g_init * sizeof(BandRec), s));
-    if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[0], s));
-    if (dense_tma) {
-        if (gen) k_init_dense_tma<true><<<(unsigned)g_init, kInitThreads, kDenseSmem, s>>>(P);
-        else k_init_dense_tma<false><<<(unsigned)g_init, kInitThreads, kDenseSmem, s>>>(P);
-    } else if (dense) {
-        if (gen) k_init_dense<true><<<(unsigned)g_init, kDenseThreads, 0, s>>>(P);
-        else k_init_dense<false><<<(unsigned)g_init, kDenseThreads, 0, s>>>(P);
+    int64_t g;
+    if (P.dense && P.nn_width <= kRowRegs) g = grid_init(ctx, gen ? 10 : 9, kInitThreads, P.n_tiles);
+    else if (P.dense) g = grid_init(ctx, gen ? 8 : 7, kDenseThreads, P.n_tiles);
+    else g = grid_init(ctx, batched ? 1 : (gen ? 6 : 0), kInitThreads, P.n_tiles);
+    if (g > max_bands) {     // fewer, longer bands
+        const int64_t per = (P.n_tiles + max_bands - 1) / max_bands;
+        g = (P.n_tiles + per - 1) / per;
+    }
+    return g;
+}
+
+ccl_status launch_init(const Params &P, bool batched, int64_t g, cudaStream_t s) {
+    const bool gen = P.gen_thr != kNoGen;
+    if (P.dense && P.nn_width <= kRowRegs) {
+        if (gen) k_init_dense_tma<true><<<(unsigned)g, kInitThreads, kDenseSmem, s>>>(P);
+        else k_init_dense_tma<false><<<(unsigned)g, kInitThreads, kDenseSmem, s>>>(P);
+    } else if (P.dense) {
+        if (gen) k_init_dense<true><<<(unsigned)g, kDenseThreads, 0, s>>>(P);
+        else k_init_dense<false><<<(unsigned)g, kDenseThreads, 0, s>>>(P);
     } else if (batched) {
-        k_init<true><<<(unsigned)g_init, kInitThreads, kInitSmem, s>>>(P);
+        k_init<true><<<(unsigned)g, kInitThreads, kInitSmem, s>>>(P);
     } else if (gen) {
-        k_init<false, true><<<(unsigned)g_init, kInitThreads, kInitSmem, s>>>(P);
+        k_init<false, true><<<(unsigned)g, kInitThreads, kInitSmem, s>>>(P);
     } else {
-        k_init<false><<<(unsigned)g_init, kInitThreads, kInitSmem, s>>>(P);
+        k_init<false><<<(unsigned)g, kInitThreads, kInitSmem, s>>>(P);
     }
     CCL_CUDA(cudaGetLastError());
+    return CCL_OK;
+}
+
+// Steps (ii)-(iv) after step (i) has filled P.n_bands band records.
+ccl_status enqueue_tail(ccl_context *ctx, const Params &P, bool batched, const TuneChoice &tc, cudaStream_t s,
+                        bool profile) {
+    const int T = tc.threads;
+    const int64_t warps_chunks = (P.n_chunks + kAnaChunks - 1) / kAnaChunks;
+    const int64_t g_red = (int64_t)ctx->num_sms * blocks_per_sm(ctx, batched ? 5 : 4, 256);
     if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[1], s));
     auto analysis = [&]() {
         const unsigned g = (unsigned)grid_for(ctx, batched ? 3 : 2, tc, warps_chunks);
@@ -327,6 +338,21 @@ ccl_status enqueue_steps(ccl_context *ctx, const Params &P0, bool batched, const
     CCL_CUDA(cudaGetLastError());
     if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[4], s));
     return CCL_OK;
+}
+
+// Enqueues the four steps. All kernels read their sizes from Params, so the
+// sequence contains no host synchronisation and can be captured.
+ccl_status enqueue_steps(ccl_context *ctx, const Params &P0, bool batched, const TuneChoice &tc,
+                         cudaStream_t s, bool profile) {
+    Params P = P0;
+    const int64_t g_init = init_grid(ctx, P, batched, kMaxBands);
+    P.n_bands = (int32_t)g_init;
+    CCL_CUDA(cudaMemsetAsync(P.counters, 0, 4 * sizeof(unsigned long long), s));
+    CCL_CUDA(cudaMemsetAsync(P.band, 0, (size_t)g_init * sizeof(BandRec), s));
+    if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[0], s));
+    ccl_status st = launch_init(P, batched, g_init, s);
+    if (st != CCL_OK) return st;
+    return enqueue_tail(ctx, P, batched, tc, s, profile);
 }
 
 uint64_t fnv1a(const void *data, size_t bytes, uint64_t h = 1469598103934665603ull) {
@@ -705,6 +731,8 @@ void ccl_context_destroy(ccl_context *ctx) {
     if (ctx->h_insts) cudaFreeHost(ctx->h_insts);
     if (ctx->d_host_in) cudaFree(ctx->d_host_in);
     if (ctx->d_aux) cudaFree(ctx->d_aux);
+    for (auto &e : ctx->part_ev) if (e) cudaEventDestroy(e);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->staging_free) cudaEventDestroy(ctx->staging_free);
     for (auto &set : ctx->prof)
         for (auto &e : set) if (e) cudaEventDestroy(e);
@@ -1004,6 +1032,81 @@ ccl_status ccl_sync(ccl_context *ctx, void *stream, int64_t timeout_ms) {
     return CCL_OK;
 }
 
+namespace {
+constexpr int kHostParts = 4;        // upload parts of the host-buffer path
+
+// The host-buffer path for inputs of at least 64 tiles: the input goes up in
+// kHostParts site ranges on the copy stream, and step (i) on each range starts
+// as soon as its rows, columns and bits have arrived (step (i) reads only the
+// rows of its own tiles), so the upload of the later ranges overlaps it.
+// Steps (ii)-(iv) then run once over all band records.
+ccl_status label_host_parts(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
+                            const int32_t *col_idx, const uint32_t *bits, int32_t *d_rp, int32_t *d_ci,
+                            uint32_t *d_bits, int32_t *d_lab, cudaStream_t s, const TuneChoice &tc) {
+    if (!ctx->copy_stream) {
+        CCL_CUDA(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+        for (auto &e : ctx->part_ev) CCL_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    const int64_t tiles = ((int64_t)n + kTileSites - 1) / kTileSites;
+    int64_t ts[kHostParts + 1], es[kHostParts + 1];       // part boundaries: tiles, CSR entries
+    for (int k = 0; k <= kHostParts; ++k) {
+        ts[k] = tiles * k / kHostParts;
+        es[k] = row_ptr[std::min<int64_t>(ts[k] * kTileSites, n)];
+        if (es[k] < 0 || es[k] > nnz || (k > 0 && es[k] < es[k - 1])) return CCL_ERR_INVALID_ARGUMENT;
+    }
+    ccl_status st = ensure_workspace(ctx, nnz, false);
+    if (st != CCL_OK) return st;
+    Params P = base_params(ctx, tc);
+    P.K = 1;
+    P.n_chunks = ((int64_t)n + kChunk - 1) / kChunk;
+    P.one.row_ptr = d_rp;
+    P.one.col_idx = d_ci;
+    P.one.bits = d_bits;
+    P.one.labels = d_lab;
+    set_bounds(P.one, d_rp, (int64_t)n + 1, d_ci, nnz, d_bits, (nnz + 31) / 32);
+    P.one.n = n;
+    P.one.nnz = (int32_t)nnz;
+    ctx->last.n_sites = n;
+    ctx->last.nnz = nnz;
+    ctx->last.n_inst = 1;
+    ctx->last.used_graph = 0;
+    CCL_CUDA(cudaMemsetAsync(P.counters, 0, 4 * sizeof(unsigned long long), s));
+    CCL_CUDA(cudaMemsetAsync(P.band, 0, (size_t)kMaxBands * sizeof(BandRec), s));
+    // the uploads may not overwrite the buffers before earlier work on s is done
+    CCL_CUDA(cudaEventRecord(ctx->part_ev[kHostParts], s));
+    CCL_CUDA(cudaStreamWaitEvent(ctx->copy_stream, ctx->part_ev[kHostParts], 0));
+    int32_t band_off = 0;
+    for (int k = 0; k < kHostParts; ++k) {
+        const int64_t t0 = ts[k], t1 = ts[k + 1];
+        const int64_t s0 = t0 * kTileSites, s1 = std::min<int64_t>(t1 * kTileSites, n);
+        const int64_t e0 = es[k], e1 = es[k + 1];
+        CCL_CUDA(cudaMemcpyAsync(d_rp + s0, row_ptr + s0, (size_t)(s1 - s0 + 1) * 4, cudaMemcpyHostToDevice,
+                                 ctx->copy_stream));
+        if (e1 > e0) {
+            CCL_CUDA(cudaMemcpyAsync(d_ci + e0, col_idx + e0, (size_t)(e1 - e0) * 4, cudaMemcpyHostToDevice,
+                                     ctx->copy_stream));
+            const int64_t w0 = e0 >> 5, w1 = ((e1 - 1) >> 5) + 1;
+            CCL_CUDA(cudaMemcpyAsync(d_bits + w0, bits + w0, (size_t)(w1 - w0) * 4, cudaMemcpyHostToDevice,
+                                     ctx->copy_stream));
+        }
+        CCL_CUDA(cudaEventRecord(ctx->part_ev[k], ctx->copy_stream));
+        CCL_CUDA(cudaStreamWaitEvent(s, ctx->part_ev[k], 0));
+        P.tile_off = t0;
+        P.n_tiles = t1 - t0;
+        P.band_off = band_off;
+        const int64_t g = init_grid(ctx, P, false, kMaxBands / kHostParts);
+        st = launch_init(P, false, g, s);
+        if (st != CCL_OK) return st;
+        band_off += (int32_t)g;
+    }
+    P.tile_off = 0;
+    P.n_tiles = tiles;
+    P.band_off = 0;
+    P.n_bands = band_off;
+    return enqueue_tail(ctx, P, false, tc, s, false);
+}
+}  // namespace
+
 ccl_status ccl_label_host(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
                           const int32_t *col_idx, const uint32_t *bits, int32_t *labels,
                           void *stream) {
@@ -1030,13 +1133,18 @@ ccl_status ccl_label_host(ccl_context *ctx, int32_t n, int64_t nnz, const int32_
     int32_t *d_ci = (int32_t *)(base + al(b_rp));
     uint32_t *d_bits = (uint32_t *)(base + al(b_rp) + al(b_ci));
     int32_t *d_lab = (int32_t *)(base + al(b_rp) + al(b_ci) + al(b_bits));
-    CCL_CUDA(cudaMemcpyAsync(d_rp, row_ptr, b_rp, cudaMemcpyHostToDevice, s));
-    if (nnz > 0) {
-        CCL_CUDA(cudaMemcpyAsync(d_ci, col_idx, b_ci, cudaMemcpyHostToDevice, s));
-        CCL_CUDA(cudaMemcpyAsync(d_bits, bits, b_bits, cudaMemcpyHostToDevice, s));
-    }
     const TuneChoice tc = choice_for(ctx, n, nnz);
-    st = label_single(ctx, n, nnz, d_rp, nnz ? d_ci : nullptr, nnz ? d_bits : nullptr, d_lab, s, tc);
+    const int64_t tiles = ((int64_t)n + kTileSites - 1) / kTileSites;
+    if (tiles >= 64 && nnz > 0 && !ctx->profile && !stream_capturing(s)) {
+        st = label_host_parts(ctx, n, nnz, row_ptr, col_idx, bits, d_rp, d_ci, d_bits, d_lab, s, tc);
+    } else {
+        CCL_CUDA(cudaMemcpyAsync(d_rp, row_ptr, b_rp, cudaMemcpyHostToDevice, s));
+        if (nnz > 0) {
+            CCL_CUDA(cudaMemcpyAsync(d_ci, col_idx, b_ci, cudaMemcpyHostToDevice, s));
+            CCL_CUDA(cudaMemcpyAsync(d_bits, bits, b_bits, cudaMemcpyHostToDevice, s));
+        }
+        st = label_single(ctx, n, nnz, d_rp, nnz ? d_ci : nullptr, nnz ? d_bits : nullptr, d_lab, s, tc);
+    }
     if (st != CCL_OK) return st;
     CCL_CUDA(cudaMemcpyAsync(labels, d_lab, b_lab, cudaMemcpyDeviceToHost, s));
     return ccl_sync(ctx, stream, -1);

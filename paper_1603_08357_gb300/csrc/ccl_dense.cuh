@@ -70,7 +70,7 @@ template <bool kGen>
 __global__ void __launch_bounds__(kDenseThreads) k_init_dense(Params P) {
     __shared__ unsigned long long band_cnt;
     int64_t band_lo, band_hi;
-    cta_band(P.n_tiles, band_lo, band_hi);
+    cta_band(P, band_lo, band_hi);
     const int64_t n = P.one.n;
     const int W = (int)P.nn_width;
     const int64_t n_words = ((int64_t)W * n + 31) >> 5;
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_init_dense(Params P) {
     const int64_t qband = s_lo * W;
     if (threadIdx.x == 0) {
         band_cnt = 0;
-        P.band[blockIdx.x].qbase = qband;
+        P.band[P.band_off + blockIdx.x].qbase = qband;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_init_dense(Params P) {
     if (bad) raise_err(P.err, kErrIndex);
     if (lane == 0 && my_pairs) {
         atomicAdd(P.counters, my_pairs);
-        atomicAdd(&P.band[blockIdx.x].cnt, my_pairs);
+        atomicAdd(&P.band[P.band_off + blockIdx.x].cnt, my_pairs);
     }
 }
 
@@ -220,14 +220,14 @@ constexpr size_t kDenseSmem = 64 + sizeof(DenseStage) * kStages;
 template <bool kGen>
 __device__ __forceinline__ void dense_produce(const Params &P, DenseStage *st, uint64_t *full, uint64_t *empty) {
     int64_t band_lo, band_hi;
-    cta_band(P.n_tiles, band_lo, band_hi);
+    cta_band(P, band_lo, band_hi);
     const int64_t n = P.one.n;
     const int W = (int)P.nn_width;
     const int64_t n_words = ((int64_t)W * n + 31) >> 5;
     const int32_t *nn_end = P.nn + (int64_t)W * n;
     const uint32_t *bits_end = kGen ? nullptr : P.one.bits + n_words;
     const int64_t qband = min(band_lo * kTileSites, n) * W;
-    if (band_lo < band_hi) P.band[blockIdx.x].qbase = qband;
+    if (band_lo < band_hi) P.band[P.band_off + blockIdx.x].qbase = qband;
     int64_t t_local = 0;
     for (int64_t tile = band_lo; tile < band_hi; ++tile, ++t_local) {
         const int s = (int)(t_local % kStages);
@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init_dense_tma(Params P) {
     }
     unsigned long long my_pairs = 0;
     int64_t band_lo, band_hi;
-    cta_band(P.n_tiles, band_lo, band_hi);
+    cta_band(P, band_lo, band_hi);
     int64_t t_local = 0;
     for (int64_t tile = band_lo; tile < band_hi; ++tile, ++t_local) {
         const int s = (int)(t_local % kStages);
@@ -503,7 +503,7 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init_dense_tma(Params P) {
     }
     if (lane == 0 && my_pairs) {
         atomicAdd(P.counters, my_pairs);
-        atomicAdd(&P.band[blockIdx.x].cnt, my_pairs);
+        atomicAdd(&P.band[P.band_off + blockIdx.x].cnt, my_pairs);
     }
 }
 

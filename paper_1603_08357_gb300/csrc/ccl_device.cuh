@@ -154,18 +154,21 @@ __device__ __forceinline__ void copy_window(const void *arr, int64_t lo, int64_t
 // label[i] = min(lower) or i; every other entry of `lower` (one occurrence of
 // the minimum removed) is a residual pair (i, j).
 
-// tiles of CTA b: the contiguous band [band_lo, band_hi)
-__device__ __forceinline__ void cta_band(int64_t n_tiles, int64_t &band_lo, int64_t &band_hi) {
-    const int64_t per = (n_tiles + gridDim.x - 1) / gridDim.x;
-    band_lo = min((int64_t)blockIdx.x * per, n_tiles);
-    band_hi = min(band_lo + per, n_tiles);
+// tiles of CTA b: the contiguous band [band_lo, band_hi) of the launch's
+// P.n_tiles tiles, which start at tile P.tile_off (0 unless step (i) runs in
+// parts); its band record is P.band[P.band_off + b]
+__device__ __forceinline__ void cta_band(const Params &P, int64_t &band_lo, int64_t &band_hi) {
+    const int64_t per = (P.n_tiles + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = min((int64_t)blockIdx.x * per, P.n_tiles);
+    band_lo = P.tile_off + lo;
+    band_hi = P.tile_off + min(lo + per, P.n_tiles);
 }
 
 template <bool kBatched, bool kGen = false>
 __device__ __forceinline__ void init_produce(const Params &P, Stage *st, uint64_t *full,
                                              uint64_t *empty) {
     int64_t band_lo, band_hi;
-    cta_band(P.n_tiles, band_lo, band_hi);
+    cta_band(P, band_lo, band_hi);
     int64_t t_local = 0;
     int64_t qband = 0;
     int kc = 0;                              // cached instance and its tile range
@@ -193,7 +196,7 @@ __device__ __forceinline__ void init_produce(const Params &P, Stage *st, uint64_
         h.status = (h.e0 < 0 || h.e1 < h.e0 || h.e1 > I.nnz) ? 1 : 0;
         if (t_local == 0) {
             qband = I.q_off + (h.status ? 0 : h.e0);
-            P.band[blockIdx.x].qbase = qband;
+            P.band[P.band_off + blockIdx.x].qbase = qband;
         }
         h.qband = qband;
         int64_t lo, hi;
@@ -482,7 +485,7 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
     }
     unsigned long long my_pairs = 0;
     int64_t band_lo, band_hi;
-    cta_band(P.n_tiles, band_lo, band_hi);
+    cta_band(P, band_lo, band_hi);
     int64_t t_local = 0;
     for (int64_t tile = band_lo; tile < band_hi; ++tile, ++t_local) {
         const int s = (int)(t_local % kStages);
@@ -540,7 +543,7 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
     }
     if (lane == 0 && my_pairs) {
         atomicAdd(P.counters, my_pairs);
-        atomicAdd(&P.band[blockIdx.x].cnt, my_pairs);
+        atomicAdd(&P.band[P.band_off + blockIdx.x].cnt, my_pairs);
     }
 }
 

@@ -85,6 +85,9 @@ struct Params {
     uint64_t gen_thr;          // ... and threshold (bond open iff output >> 11 < gen_thr)
     const int32_t *nn;         // dense neighbour list (slot k of site i at nn[i + k*n]), or null
     int64_t nn_width;          // slots per site of the dense list
+    int64_t tile_off;          // step (i) on part of the tiles: its first tile ...
+    int32_t band_off;          // ... and its first band record
+    int32_t pad2_;
     unsigned *err;
     unsigned long long *counters;   // [0] residual pairs
 };

@@ -343,3 +343,26 @@ def test_tune_cache_file_roundtrip(tmp_path, monkeypatch):
         assert np.array_equal(out.cpu().numpy(), want)
     finally:
         ccl.ccl_context_destroy(c)
+
+
+@pytest.mark.parametrize("L_", [255, 256, 257, 700])
+def test_host_path_parts(ctx, L_):
+    """The host-buffer entry point uploads large inputs in parts and starts
+    step (i) on each part as it arrives; sizes around the 64-tile threshold,
+    ragged tails, and a multigraph with rows of every length."""
+    for lat in (L.triangle(L_, L.PC_TRIANGLE, 4), L.random_graph(L_ * L_, 2 * L_ * L_, 5)):
+        out = np.full(lat.n, -1, np.int32)
+        st = ccl.ccl_label_host(ctx, lat.n, lat.nnz, lat.row_ptr, lat.col_idx, lat.open_bits, out)
+        assert st == ccl.CCL_OK, ccl.ccl_status_string(st)
+        assert np.array_equal(out, oracle.uf_label(lat))
+
+
+def test_host_path_bad_row_ptr(ctx):
+    lat = L.triangle(400, 0.4, 6)
+    rp = lat.row_ptr.copy()
+    rp[lat.n // 2] = lat.nnz + 5                     # past the entries: rejected before any launch
+    out = np.empty(lat.n, np.int32)
+    st = ccl.ccl_label_host(ctx, lat.n, lat.nnz, rp, lat.col_idx, lat.open_bits, out)
+    assert st in (ccl.CCL_ERR_INVALID_ARGUMENT, ccl.CCL_ERR_INDEX_OUT_OF_RANGE)
+    assert ccl.ccl_label_host(ctx, lat.n, lat.nnz, lat.row_ptr, lat.col_idx, lat.open_bits, out) == ccl.CCL_OK
+    assert np.array_equal(out, oracle.uf_label(lat))
