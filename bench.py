@@ -121,20 +121,36 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------
-# oracle timing (CPU baseline / reference arm)
+# The CPU-baseline leg and the reference arm: the only places that run the
+# oracle. The leg also compares the GPU's labels with the oracle's labels of the
+# same input, which it computes anyway.
 
-def oracle_time(lat, budget_s: float, min_reps: int = 1):
+def oracle_time(lat, budget_s: float, min_reps: int = 1, check=None):
     """Times the oracle's union-find labelling of the full instance on one core,
-    repeating until `budget_s` seconds have elapsed; returns (sites/s, reps, secs)."""
+    repeating until `budget_s` seconds have elapsed; returns (sites/s, reps,
+    secs, same) with same = whether `check` equals the oracle's labels (None
+    without `check`)."""
     import oracle
     reps, t0 = 0, time.perf_counter()
+    labels = None
     while True:
-        oracle.uf_label(lat)
+        labels = oracle.uf_label(lat)
         reps += 1
         el = time.perf_counter() - t0
         if reps >= min_reps and el >= budget_s:
             break
-    return lat.n * reps / el, reps, el
+    same = None if check is None else bool(np.array_equal(check, labels))
+    return lat.n * reps / el, reps, el, same
+
+
+def oracle_input(lat, seed=None):
+    """The instance the oracle labels: lat itself, or (bonds drawn on the
+    device) lat with the open bits of realisation (seed, lat.p)."""
+    if seed is None:
+        return lat
+    import dataclasses
+    import oracle
+    return dataclasses.replace(lat, open_bits=oracle.keyed_bits(lat, seed, lat.p))
 
 
 def replica_spec(name: str, rank: int) -> dict:
@@ -421,17 +437,7 @@ def run_ours(args, rank, world, local):
         e2e_step()
     e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / e_steps, dist, dev)
 
-    # parity guard on the labels of the last timed step (full comparison in tests)
-    import oracle
-    if lat.n > 60_000_000:
-        ok_sample = None
-    elif kind in ("random", "dense-random"):
-        import dataclasses
-        want = oracle.uf_label(dataclasses.replace(lat, open_bits=oracle.keyed_bits(lat, last_seed, lat.p)))
-        ok_sample = bool(np.array_equal(last_labels, want))
-    else:
-        ok_sample = bool(np.array_equal(last_labels, oracle.uf_label(lat)))
-
+    ok_sample = None
     if rank == 0:
         peak, peak_src = _peaks()
         ab = algorithmic_bytes(lat.n, lat.nnz, q, kind, width)
@@ -443,7 +449,9 @@ def run_ours(args, rank, world, local):
         traffic, scaled = _ncu_traffic(dom_name, workload)
         cpu = None
         if not args.no_cpu_baseline:
-            v, reps, secs = oracle_time(lat, args.cpu_seconds)
+            # the leg's oracle labels also check the labels of the last timed step
+            ref = oracle_input(lat, last_seed if kind in ("random", "dense-random") else None)
+            v, reps, secs, ok_sample = oracle_time(ref, args.cpu_seconds, check=last_labels)
             cpu = {"value": v, "unit": "sites/s", "cores": 1, "kind": "oracle",
                    "sample": f"union-find oracle over the full instance ({lat.n} sites), "
                              f"{reps} pass(es) in {secs:.1f} s, 1 thread"}
@@ -478,7 +486,7 @@ def run_ours(args, rank, world, local):
                     "entry": entry},
             "gpu_launches": args.steps * (4 if opts["pre_analysis"] else 3),
             "clocks": clk,
-            "parity_last_step": ok_sample,
+            "parity_last_step": ok_sample,      # from the CPU-baseline leg (None without it)
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -491,7 +499,6 @@ def run_batched(args, rank, world, local):
     steps (ccl_label_batched, graph replay), against the same instances
     labelled one ccl_label call at a time."""
     import torch
-    import oracle
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -572,26 +579,28 @@ def run_batched(args, rank, world, local):
     ms_one = max_over_ranks(e0.elapsed_time(e1) / reps, dist, dev)
     same = bool(torch.equal(out1, labels))
 
-    # parity: a seeded sample of instances against the oracle
+    # a seeded sample of instances for the CPU-baseline leg (and its parity check)
     rng = np.random.default_rng(11 + rank)
     sample = sorted(rng.choice(b.k, size=min(args.parity_sample, b.k), replace=False).tolist())
-    ok = True
-    for k in sample:
-        s0, s1 = int(so[k]), int(so[k + 1])
-        if not np.array_equal(got[s0:s1], oracle.uf_label(b.instance(k))):
-            ok = False
+    ok = None
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
+            import oracle
             inst = [b.instance(k) for k in sample]      # built before the clock starts
             t0, done, sites = time.perf_counter(), 0, 0
-            for lat in inst:
-                oracle.uf_label(lat)
+            want = {}
+            for k, lat in zip(sample, inst):
+                want[k] = oracle.uf_label(lat)
                 sites += lat.n
                 done += 1
                 if time.perf_counter() - t0 > args.cpu_seconds:
                     break
             el = time.perf_counter() - t0
+            for k, lat in zip(sample, inst):           # the rest of the sample, untimed
+                if k not in want:
+                    want[k] = oracle.uf_label(lat)
+            ok = all(np.array_equal(got[int(so[k]):int(so[k + 1])], want[k]) for k in sample)
             cpu = {"value": sites / el, "unit": "sites/s", "cores": 1, "kind": "oracle",
                    "sample": f"union-find oracle over {done} instances of the batch ({sites} sites), 1 thread"}
         line = {
@@ -626,7 +635,6 @@ def run_served(args, rank, world, local):
     Requests repeat a pool of distinct pre-generated instances (the whole
     stream would not fit in host memory)."""
     import torch
-    import oracle
     torch.cuda.set_device(local)
     import paper_1603_08357_gb300 as ccl
     t_gen = time.perf_counter()
@@ -737,10 +745,11 @@ def run_served(args, rank, world, local):
                             "p50_ms": so.p50_ms, "p99_ms": so.p99_ms, "max_ms": so.max_ms,
                             "batches": int(so.batches)}
 
-    ok = all(np.array_equal(buf, oracle.uf_label(req[k])) for kp in (keep, keep_copy) for k, buf in kp.items())
+    ok = None
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
+            import oracle
             t2, sites, done = time.perf_counter(), 0, 0
             for lat in pool:
                 oracle.uf_label(lat)
@@ -750,6 +759,8 @@ def run_served(args, rank, world, local):
                     break
             cpu = {"value": sites / (time.perf_counter() - t2), "unit": "sites/s", "cores": 1,
                    "kind": "oracle", "sample": f"union-find oracle over {done} pool requests ({sites} sites), 1 thread"}
+            # the leg's oracle also checks the kept labels of both submission modes
+            ok = all(np.array_equal(buf, oracle.uf_label(req[k])) for kp in (keep, keep_copy) for k, buf in kp.items())
         h2d = sum(4 * (lat.n + 1) + 4 * lat.nnz + 4 * lat.open_bits.size for lat in req) / len(req)
         line = {
             "metric": "sites labeled/s (served)", "value": world * capacity, "unit": "sites/s",
