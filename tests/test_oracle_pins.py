@@ -117,6 +117,11 @@ def test_random_graphs_agree_and_invariants(seed):
     assert np.array_equal(o1, expect)
     idx = np.arange(lat.n)
     assert np.all(o1 <= idx) and np.array_equal(o1[o1], o1)
+    # every open bond's ends share a label, and a label is the least site carrying it
+    assert np.array_equal(o1[u[keep]], o1[v[keep]])
+    least = np.full(lat.n, lat.n, np.int64)
+    np.minimum.at(least, o1, idx)
+    assert np.array_equal(least[o1], o1)
 
 
 @pytest.mark.parametrize("z,S,p,perm", [(3, 8, 0.5, None), (3, 8, 0.5, 9), (4, 6, 0.4, 5),
