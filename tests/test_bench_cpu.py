@@ -1,0 +1,58 @@
+"""Host logic of bench.py that needs no GPU: the algorithmic byte counts of
+each input kind, the CPU-baseline leg's timing and label check, and the
+reference arm's JSON line."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+import lattices as L  # noqa: E402
+
+
+def test_algorithmic_bytes_by_input_kind():
+    n, nnz, q, W = 1000, 6000, 300, 6
+    csr = bench.algorithmic_bytes(n, nnz, q)
+    assert csr["init"] == 4 * (n + 1) + 4 * nnz + 4 * ((nnz + 31) // 32) + 4 * n + 8 * q
+    assert csr["analysis_ii"] == csr["analysis_iv"] == 8 * n
+    assert csr["reduce"] == 16 * q
+    assert csr["path"] == csr["init"] + 2 * 8 * n + 16 * q
+    rnd = bench.algorithmic_bytes(n, nnz, q, "random")
+    assert csr["init"] - rnd["init"] == 4 * ((nnz + 31) // 32)       # no bit words read
+    dense = bench.algorithmic_bytes(n, nnz, q, "dense", W)
+    assert dense["init"] == 4 * W * n + 4 * ((W * n + 31) // 32) + 4 * n + 8 * q
+    assert bench.algorithmic_bytes(n, nnz, q, "dense-random", W)["init"] == 4 * W * n + 4 * n + 8 * q
+
+
+def test_cpu_leg_checks_labels():
+    import oracle
+    lat = L.triangle(40, 0.4, 3)
+    good = oracle.uf_label(lat)
+    v, reps, secs, same = bench.oracle_time(lat, 0.0, check=good)
+    assert v > 0 and reps >= 1 and same is True
+    bad = good.copy()
+    bad[5] = 5 if good[5] != 5 else 4
+    assert bench.oracle_time(lat, 0.0, check=bad)[3] is False
+    assert bench.oracle_time(lat, 0.0)[3] is None
+    # device-drawn bonds: the leg labels the keyed realisation
+    ref = bench.oracle_input(lat, 99)
+    assert not np.array_equal(ref.open_bits, lat.open_bits)
+    assert np.array_equal(ref.open_bits, oracle.keyed_bits(lat, 99, lat.p))
+
+
+def test_reference_arm_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--config",
+                        "hc256", "--steps", "2", "--warmup", "1"], capture_output=True, text=True, timeout=600,
+                       cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == "sites labeled/s" and line["unit"] == "sites/s"
+    assert line["value"] > 0 and line["higher_is_better"] is True and line["steps"] == 2
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert line["config"]["workload"] == "hc256"
