@@ -448,7 +448,7 @@ def run_ours(args, rank, world, local):
         workload = args.config if kind == "csr" else f"{args.config}/{kind}"
         traffic, scaled = _ncu_traffic(dom_name, workload)
         cpu = None
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and world == 1:      # the CPU baseline is an N=1 figure
             # the leg's oracle labels also check the labels of the last timed step
             ref = oracle_input(lat, last_seed if kind in ("random", "dense-random") else None)
             v, reps, secs, ok_sample = oracle_time(ref, args.cpu_seconds, check=last_labels)
@@ -585,7 +585,7 @@ def run_batched(args, rank, world, local):
     ok = None
     if rank == 0:
         cpu = None
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and world == 1:      # the CPU baseline is an N=1 figure
             import oracle
             inst = [b.instance(k) for k in sample]      # built before the clock starts
             t0, done, sites = time.perf_counter(), 0, 0
@@ -748,7 +748,7 @@ def run_served(args, rank, world, local):
     ok = None
     if rank == 0:
         cpu = None
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and world == 1:      # the CPU baseline is an N=1 figure
             import oracle
             t2, sites, done = time.perf_counter(), 0, 0
             for lat in pool:
