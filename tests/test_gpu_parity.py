@@ -366,3 +366,44 @@ def test_host_path_bad_row_ptr(ctx):
     assert st in (ccl.CCL_ERR_INVALID_ARGUMENT, ccl.CCL_ERR_INDEX_OUT_OF_RANGE)
     assert ccl.ccl_label_host(ctx, lat.n, lat.nnz, lat.row_ptr, lat.col_idx, lat.open_bits, out) == ccl.CCL_OK
     assert np.array_equal(out, oracle.uf_label(lat))
+
+
+def test_thousands_of_small_random_graphs():
+    """2000 random multigraphs of 1..300 sites (self-loops, repeated edges,
+    isolated sites) labelled in one batched call, each against the oracle."""
+    from ccl_testutil import batch_to_dev
+    rng = np.random.default_rng(77)
+    lats = []
+    for k in range(2000):
+        n = int(rng.integers(1, 301))
+        m = int(rng.integers(0, 2 * n + 1))
+        lats.append(L.random_graph(n, m, 1000 + k, p=float(rng.uniform(0.2, 0.9))))
+    K = len(lats)
+    site_off = np.zeros(K + 1, np.int64)
+    ent_off = np.zeros(K + 1, np.int64)
+    site_off[1:] = np.cumsum([x.n for x in lats])
+    ent_off[1:] = np.cumsum([x.nnz for x in lats])
+    row_ptr = np.concatenate([x.row_ptr for x in lats]).astype(np.int32)        # n_k + 1 each
+    col_idx = np.concatenate([x.col_idx for x in lats]).astype(np.int32)
+    bitv = np.concatenate([L.unpack_bits(x.open_bits, x.nnz) for x in lats])
+    b = L.Batch(site_off, ent_off, row_ptr, col_idx, L.pack_bits(bitv), [{"kind": "random"}] * K)
+    assert b.k == K and b.n_total == int(site_off[-1])
+    c = ccl.ccl_context_create(0)
+    try:
+        got = gpu_label_batched(c, b)
+    finally:
+        ccl.ccl_context_destroy(c)
+    for k, x in enumerate(lats):
+        assert np.array_equal(got[int(site_off[k]):int(site_off[k + 1])], oracle.uf_label(x)), k
+
+
+def test_allocation_failure_is_reported_and_recoverable():
+    """A workspace the device cannot hold (16 TB of pair slots) is refused with
+    CCL_ERR_OUT_OF_MEMORY; the context keeps labelling afterwards."""
+    c = ccl.ccl_context_create(0)
+    try:
+        assert ccl.ccl_reserve(c, 0, 1 << 41, 0) == ccl.CCL_ERR_OUT_OF_MEMORY
+        lat = L.triangle(300, 0.4, 8)
+        assert np.array_equal(gpu_label(c, lat), oracle.uf_label(lat))
+    finally:
+        ccl.ccl_context_destroy(c)
