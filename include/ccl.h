@@ -359,6 +359,7 @@ typedef struct {
     double p50_ms, p99_ms, max_ms;   /* submit -> labels on host */
     double busy_seconds;             /* wall time from first submit to last completion */
     double sites_per_second;
+    int64_t waiting;                 /* threads inside ccl_server_wait now */
 } ccl_server_stats;
 
 /* Starts the server thread. cfg may be NULL for defaults. */
@@ -382,7 +383,11 @@ CCL_API ccl_status ccl_server_wait(ccl_server *srv, uint64_t ticket, int32_t *la
 
 CCL_API ccl_status ccl_server_stats_get(ccl_server *srv, ccl_server_stats *stats);
 
-/* Stops the thread; requests not yet completed are dropped. */
+/* Stops the server's threads. Batches already on the device finish; requests
+ * not yet launched are dropped: a ccl_server_wait blocked on one in another
+ * thread returns CCL_ERR_REJECTED without writing labels_host, and destroy
+ * returns only after every such waiter has left. No call may use srv once
+ * destroy has started, except those waits already in progress. */
 CCL_API void ccl_server_destroy(ccl_server *srv);
 
 #ifdef __cplusplus

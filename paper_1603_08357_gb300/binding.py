@@ -71,7 +71,8 @@ class ccl_server_stats(ctypes.Structure):
                 ("rejected", ctypes.c_int64), ("batches", ctypes.c_int64),
                 ("sites_completed", ctypes.c_int64), ("p50_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
-                ("busy_seconds", ctypes.c_double), ("sites_per_second", ctypes.c_double)]
+                ("busy_seconds", ctypes.c_double), ("sites_per_second", ctypes.c_double),
+                ("waiting", ctypes.c_int64)]
 
 
 def _load() -> ctypes.CDLL:

@@ -66,6 +66,7 @@ struct Req {
     Clock::time_point t_submit, t_done;
     ccl_status status = CCL_OK;
     bool done = false;
+    bool dropped = false;   // ended by ccl_server_destroy before it was labelled
 };
 
 struct Batch {
@@ -227,6 +228,7 @@ struct ccl_server {
     std::map<uint64_t, std::shared_ptr<Req>> tickets;
     uint64_t next_ticket = 1;
     bool stop = false;
+    int waiters = 0;        // threads inside ccl_server_wait (destroy waits for them to leave)
 
     // uploads in flight (uploader thread pushes, server thread pops; under mu)
     std::deque<std::shared_ptr<Req>> uploading;
@@ -620,9 +622,23 @@ ccl_status ccl_server_wait(ccl_server *S, uint64_t ticket, int32_t *labels_host,
     auto it = S->tickets.find(ticket);
     if (it == S->tickets.end()) return CCL_ERR_NOT_FOUND;
     auto r = it->second;
+    // counted while inside, so that ccl_server_destroy frees nothing under a waiter
+    ++S->waiters;
+    struct Leave {
+        ccl_server *S;
+        std::unique_lock<std::mutex> &lk;
+        ~Leave() {
+            if (!lk.owns_lock()) lk.lock();
+            if (--S->waiters == 0) S->cv_done.notify_all();
+        }
+    } leave{S, lk};
     auto ready = [&] { return r->done; };
     if (timeout_ms < 0) S->cv_done.wait(lk, ready);
     else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) return CCL_ERR_TIMEOUT;
+    if (r->dropped) {
+        S->tickets.erase(ticket);
+        return r->status;
+    }
     if (labels_host && r->n > 0) {
         // copy outside the lock: the request is done and only this waiter owns it now
         S->tickets.erase(ticket);
@@ -648,6 +664,7 @@ ccl_status ccl_server_stats_get(ccl_server *S, ccl_server_stats *out) {
     out->rejected = S->rejected;
     out->batches = S->batches;
     out->sites_completed = S->sites_completed;
+    out->waiting = S->waiters;
     if (!S->lat_ms.empty()) {
         std::vector<double> v = S->lat_ms;
         std::sort(v.begin(), v.end());
@@ -674,6 +691,20 @@ void ccl_server_destroy(ccl_server *S) {
     for (auto &u : S->uploaders)
         if (u.joinable()) u.join();
     if (S->th.joinable()) S->th.join();
+    {
+        // requests that were never labelled end as CCL_ERR_REJECTED; waiters
+        // blocked on them return, and every waiter leaves before anything is freed
+        std::unique_lock<std::mutex> lk(S->mu);
+        for (auto &kv : S->tickets) {
+            Req &r = *kv.second;
+            if (r.done) continue;
+            r.dropped = true;
+            r.status = CCL_ERR_REJECTED;
+            r.done = true;
+        }
+        S->cv_done.notify_all();
+        S->cv_done.wait(lk, [&] { return S->waiters == 0; });
+    }
     S->copier.reset();
     cudaSetDevice(S->cfg.device);
     for (auto c : S->ctxs) ccl_context_destroy(c);
@@ -682,10 +713,6 @@ void ccl_server_destroy(ccl_server *S) {
     if (S->pool) cudaMemPoolDestroy(S->pool);
     if (S->h_stage) cudaFreeHost(S->h_stage);
     (void)cudaGetLastError();
-    {
-        std::lock_guard<std::mutex> lk(S->mu);
-        S->cv_done.notify_all();
-    }
     delete S;
 }
 

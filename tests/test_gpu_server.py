@@ -1,6 +1,7 @@
 """The request loop (continuous batching): requests submitted while others are
 on the GPU are admitted as memory frees up, batched and labelled; every result
 must equal the oracle's and the result of the same request labelled alone."""
+import ctypes
 import threading
 import time
 
@@ -141,3 +142,49 @@ def test_nocopy_requests_match_oracle():
             assert np.array_equal(_wait(srv, t, lat.n), oracle.uf_label(lat))
     finally:
         ccl.ccl_server_destroy(srv)
+
+
+def test_destroy_with_waiters_blocked():
+    """ccl_server_destroy while other threads wait on their tickets: every
+    wait returns, either with the oracle's labels (labelled before the stop)
+    or CCL_ERR_REJECTED with its output untouched (dropped), and destroy
+    returns only after the waiters have left."""
+    lat = L.triangle(2000, L.PC_TRIANGLE, 21)
+    want = oracle.uf_label(lat)
+    srv = ccl.ccl_server_create(0, n_streams=1, max_batch=1)
+    tickets = []
+    for _ in range(128):
+        st, t = ccl.ccl_server_submit_nocopy(srv, lat.n, lat.nnz, lat.row_ptr, lat.col_idx, lat.open_bits)
+        assert st == ccl.CCL_OK, ccl.ccl_status_string(st)
+        tickets.append(t)
+    watched = tickets[:4] + tickets[-28:]      # the last ones are labelled last
+    outs = [np.full(lat.n, -1, np.int32) for _ in watched]
+    status = [None] * len(watched)
+    class Handle:       # the raw handle: srv.close() clears srv's own
+        _as_parameter_ = ctypes.c_void_p(srv.handle)
+
+    def waiter(k):
+        status[k] = ccl.ccl_server_wait(Handle, watched[k], outs[k], 60_000)
+
+    threads = [threading.Thread(target=waiter, args=(k,)) for k in range(len(watched))]
+    for th in threads:
+        th.start()
+    # destroy may only overlap waits already in progress: wait until every
+    # thread is inside ccl_server_wait (or already returned)
+    deadline = time.monotonic() + 10
+    while ccl.ccl_server_stats_get(srv).waiting + sum(s is not None for s in status) < len(watched):
+        assert time.monotonic() < deadline
+        time.sleep(0.0005)
+    srv.close()
+    for th in threads:
+        th.join(timeout=10)
+        assert not th.is_alive()
+    dropped = 0
+    for st, out in zip(status, outs):
+        if st == ccl.CCL_OK:
+            assert np.array_equal(out, want)
+        else:
+            assert st == ccl.CCL_ERR_REJECTED, ccl.ccl_status_string(st)
+            assert (out == -1).all()
+            dropped += 1
+    assert dropped >= 1
