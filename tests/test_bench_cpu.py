@@ -56,3 +56,20 @@ def test_reference_arm_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
     assert line["config"]["workload"] == "hc256"
+
+
+def test_committed_traffic_is_plausible():
+    """Every per-launch DRAM figure in profiles/traffic.json lies within a
+    small factor of the bytes its workload holds (a unit slip in turning ncu's
+    Mbyte/Gbyte columns into bytes moves it by 10^3)."""
+    sizes = {"tri4096": (4096 * 4096, 6 * 4096 * 4096), "tri4096/dense": (4096 * 4096, 6 * 4096 * 4096),
+             "bethe24": (1 + 3 * (2 ** 24 - 1), 2 * 3 * (2 ** 24 - 1))}
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+        traffic = json.load(fh)
+    assert traffic
+    for key, ent in traffic.items():
+        workload = key.split(":", 1)[1]
+        n, nnz = sizes[workload]
+        held = 4 * (n + 1) + 4 * nnz + nnz // 8 + 4 * n + 8 * nnz    # inputs, labels, a full queue
+        b = ent["dram_bytes_per_launch"]
+        assert 0.05 * 8 * n <= b <= 4 * held, (key, b)
