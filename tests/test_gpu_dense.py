@@ -130,3 +130,49 @@ def test_dense_full_size_triangle(ctx):
     lat = L.triangle(4096, 0.3473, 2)
     W, nn, bits = L.to_dense(lat)
     assert np.array_equal(gpu_dense(ctx, lat.n, W, nn, bits), oracle.uf_label(lat))
+
+
+def _chorded_ring(n, chords, p, seed):
+    """Ring i -- i+1 plus chords i -- i+c (periodic), bonds open with
+    probability p; degree at most 2 + 2 * len(chords)."""
+    rng = np.random.default_rng(seed)
+    i = np.arange(n)
+    us = [i] + [i for _ in chords]
+    vs = [(i + 1) % n] + [(i + c) % n for c in chords]
+    u = np.concatenate(us); v = np.concatenate(vs)
+    keep = u != v
+    u, v = u[keep], v[keep]
+    op = rng.random(len(u)) < p
+    rows = np.concatenate([u, v]); cols = np.concatenate([v, u]); bitv = np.concatenate([op, op])
+    order = np.argsort(rows, kind="stable")
+    rows, cols, bitv = rows[order], cols[order], bitv[order]
+    rp = np.zeros(n + 1, np.int64); np.add.at(rp, rows + 1, 1)
+    return L.Lattice("ring", n, len(cols), np.cumsum(rp).astype(np.int32), cols.astype(np.int32),
+                     L.pack_bits(bitv), p, seed)
+
+
+@pytest.mark.parametrize("W", [1, 2, 7, 8, 9])
+@pytest.mark.parametrize("n", [1, 31, 1025, 70001])
+def test_dense_width_boundaries(ctx, W, n):
+    """Widths at the edges of the dense kernels (8 is the widest the staged
+    kernel takes, 9 the narrowest of the general one), used slots scattered
+    over the row, ragged site counts."""
+    if W == 1:                                              # a matching: degree 1
+        i = np.arange(0, n - 1, 2)
+        u, v = i, i + 1
+        op = np.random.default_rng(W + n).random(len(u)) < 0.6
+        rows = np.concatenate([u, v]); cols = np.concatenate([v, u]); bitv = np.concatenate([op, op])
+        order = np.argsort(rows, kind="stable")
+        rp = np.zeros(n + 1, np.int64); np.add.at(rp, rows[order] + 1, 1)
+        lat = L.Lattice("matching", n, len(cols), np.cumsum(rp).astype(np.int32),
+                        cols[order].astype(np.int32), L.pack_bits(bitv[order]), 0.6, 0)
+    else:
+        lat = _chorded_ring(n, [7, 13][: (W - 2) // 2] if W >= 4 else [], 0.45, W * 1000 + n)
+    deg = int(np.diff(lat.row_ptr).max()) if lat.n else 0
+    assert deg <= W
+    for slot_seed in (None, 3):
+        Wd, nn, bits = L.to_dense(lat, W, slot_seed)
+        assert Wd == W
+        want = oracle.dense_uf_label(lat.n, W, nn, bits)
+        assert np.array_equal(want, oracle.uf_label(lat))
+        assert np.array_equal(gpu_dense(ctx, lat.n, W, nn, bits), want)

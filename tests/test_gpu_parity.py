@@ -61,6 +61,63 @@ def test_heavy_rows_direct_path(ctx):
     assert np.array_equal(gpu_label(ctx, lat), oracle.uf_label(lat))
 
 
+def _csr_from_edges(n, u, v, op):
+    rows = np.concatenate([u, v]); cols = np.concatenate([v, u]); bitv = np.concatenate([op, op])
+    order = np.argsort(rows, kind="stable")
+    rows, cols, bitv = rows[order], cols[order], bitv[order]
+    rp = np.zeros(n + 1, np.int64); np.add.at(rp, rows + 1, 1); rp = np.cumsum(rp).astype(np.int32)
+    return L.Lattice("edges", n, len(cols), rp, cols.astype(np.int32), L.pack_bits(bitv), 0.5, 0)
+
+
+@pytest.mark.parametrize("hub_degrees", [(20000,), (9000, 9000, 40)])
+def test_tile_entries_beyond_one_stage(ctx, hub_degrees):
+    """Tiles whose CSR entries exceed what one shared-memory stage holds
+    (7168 columns): the stage holds part of the range, the rest is read from
+    global memory, and every row of the tile takes the bounds-checked path."""
+    n = 50000
+    rng = np.random.default_rng(sum(hub_degrees))
+    us, vs = [], []
+    for h, deg in enumerate(hub_degrees):
+        hub = 1500 + 3 * h                          # hubs share one 1024-site tile
+        nb = rng.choice(np.delete(np.arange(n), hub), deg, replace=False)
+        us.append(np.full(deg, hub)); vs.append(nb)
+    ring = np.arange(n - 1)
+    us.append(ring); vs.append(ring + 1)
+    u = np.concatenate(us); v = np.concatenate(vs)
+    op = rng.random(len(u)) < 0.35
+    lat = _csr_from_edges(n, u, v, op)
+    tile = lat.row_ptr[2048] - lat.row_ptr[1024]
+    assert tile > 7168
+    assert np.array_equal(gpu_label(ctx, lat), oracle.uf_label(lat))
+    assert ccl.ccl_get_stats(ctx).residual_pairs == oracle.steps_label(lat)["n_residual"]
+
+
+def test_tile_entries_beyond_one_stage_batched(ctx):
+    """The same overflowing tile inside a batch, after an instance whose entry
+    count leaves the hub instance's bits starting mid-word (bit offset not a
+    multiple of 32)."""
+    from ccl_testutil import gpu_label_batched
+    rng = np.random.default_rng(11)
+    n = 30000
+    nb = rng.choice(np.delete(np.arange(n), 1500), 15000, replace=False)
+    ring = np.arange(n - 1)
+    u = np.concatenate([np.full(15000, 1500), ring]); v = np.concatenate([nb, ring + 1])
+    hub = _csr_from_edges(n, u, v, rng.random(len(u)) < 0.4)
+    lats = [L.random_graph(37, 29, 5, p=0.6), hub, L.triangle(33, L.PC_TRIANGLE, 6)]
+    assert lats[0].nnz % 32 != 0
+    K = len(lats)
+    site_off = np.zeros(K + 1, np.int64); site_off[1:] = np.cumsum([x.n for x in lats])
+    ent_off = np.zeros(K + 1, np.int64); ent_off[1:] = np.cumsum([x.nnz for x in lats])
+    row_ptr = np.concatenate([x.row_ptr for x in lats]).astype(np.int32)
+    col_idx = np.concatenate([x.col_idx for x in lats]).astype(np.int32)
+    bitv = np.concatenate([L.unpack_bits(x.open_bits, x.nnz) for x in lats])
+    b = L.Batch(site_off, ent_off, row_ptr, col_idx, L.pack_bits(bitv), [{"kind": "edges"}] * K)
+    got = gpu_label_batched(ctx, b)
+    for k, x in enumerate(lats):
+        assert np.array_equal(got[int(site_off[k]):int(site_off[k + 1])], oracle.uf_label(x)), k
+    assert ccl.ccl_get_stats(ctx).residual_pairs == sum(oracle.steps_label(x)["n_residual"] for x in lats)
+
+
 def _lattice_cases():
     out = []
     for p in [0.0, 0.25, None, 0.75, 1.0]:

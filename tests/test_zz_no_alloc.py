@@ -12,6 +12,7 @@ import pytest
 import torch
 
 import lattices as L
+import oracle
 import paper_1603_08357_gb300 as ccl
 from ccl_testutil import DEV, gpu_label, to_dev
 
@@ -36,6 +37,23 @@ def test_noalloc_matches_ccl_label_twice(ctx):
         second = _noalloc(lat)
         assert np.array_equal(first, want)
         assert np.array_equal(second, want)
+        assert np.array_equal(first, oracle.uf_label(lat))
+
+
+def test_noalloc_at_its_limit():
+    """Exactly 2^21 CSR entries (the largest input its scratch holds): the
+    oracle's labels."""
+    rng = np.random.default_rng(21)
+    n, m = 400000, 1 << 20
+    u = rng.integers(0, n, m); v = rng.integers(0, n, m)
+    op = rng.random(m) < 0.5
+    rows = np.concatenate([u, v]); cols = np.concatenate([v, u]); bitv = np.concatenate([op, op])
+    order = np.argsort(rows, kind="stable")
+    rp = np.zeros(n + 1, np.int64); np.add.at(rp, rows[order] + 1, 1)
+    lat = L.Lattice("random", n, len(cols), np.cumsum(rp).astype(np.int32), cols[order].astype(np.int32),
+                    L.pack_bits(bitv[order]), 0.5, 21)
+    assert lat.nnz == 1 << 21
+    assert np.array_equal(_noalloc(lat), oracle.uf_label(lat))
 
 
 def test_noalloc_rejects_beyond_its_scratch():
