@@ -67,6 +67,69 @@ def test_relabel_and_sizes(ctx, kind, kw, p):
     assert ccl.ccl_relabel(ctx, lat.n, d_lab, d_lab, nc) == ccl.CCL_ERR_INVALID_ARGUMENT
 
 
+def _relabel(ctx, lab, with_sizes=True):
+    n = lab.size
+    d_lab = torch.from_numpy(lab).to(DEV) if n else torch.zeros(1, dtype=torch.int32, device=DEV)
+    seq = torch.full((max(n, 1),), -1, dtype=torch.int32, device=DEV)
+    sizes = torch.full((max(n, 1),), -1, dtype=torch.int32, device=DEV) if with_sizes else None
+    nc = torch.full((1,), -9, dtype=torch.int32, device=DEV)
+    assert ccl.ccl_relabel(ctx, n, d_lab, seq, nc, sizes) == ccl.CCL_OK
+    assert ccl.ccl_sync(ctx) == ccl.CCL_OK
+    C = int(nc.item())
+    return C, seq[:n].cpu().numpy(), (sizes[:C].cpu().numpy() if with_sizes else None)
+
+
+@pytest.mark.parametrize("n", [0, 1, 31, 8192, 8193])
+def test_relabel_block_edges(ctx, n):
+    """Site counts at the edges of the relabelling blocks (8192 sites), with
+    and without the sizes output."""
+    lat = L.random_graph(n, max(0, n // 2), 8, p=0.7) if n else None
+    lab = gpu_label(ctx, lat) if n else np.zeros(0, np.int32)
+    want_seq, want_sizes = stats.sequential(lab)
+    for with_sizes in (True, False):
+        C, seq, sizes = _relabel(ctx, lab, with_sizes)
+        assert C == want_sizes.size
+        assert np.array_equal(seq, want_seq)
+        if with_sizes:
+            assert np.array_equal(sizes, want_sizes)
+
+
+def test_relabel_more_blocks_than_scan_threads(ctx):
+    """9.4M sites: 1152 relabelling blocks, more than the one-CTA scan has
+    threads, so each scan thread sums a run of blocks."""
+    lat = L.triangle(3072, L.PC_TRIANGLE, 12)
+    lab = gpu_label(ctx, lat)
+    assert np.array_equal(lab, oracle.uf_label(lat))
+    C, seq, sizes = _relabel(ctx, lab)
+    want_seq, want_sizes = stats.sequential(lab)
+    assert (lat.n + 8191) // 8192 > 1024
+    assert C == want_sizes.size and np.array_equal(seq, want_seq) and np.array_equal(sizes, want_sizes)
+
+
+def test_spanning_empty_sets_and_bad_sites(ctx):
+    """No top (or bottom) sites: -1. Site numbers outside [0, n) are skipped
+    and reported by ccl_sync; the result is that of the valid sites."""
+    lat = L.triangle(96, 0.7, 3, periodic_y=False)
+    lab = gpu_label(ctx, lat)
+    top, bot = L.row_sites(lat, 0), L.row_sites(lat, 95)
+    want = stats.spanning_label(oracle.uf_label(lat), top, bot)
+    assert want >= 0
+    d_lab = torch.from_numpy(lab).to(DEV)
+    res = torch.zeros(1, dtype=torch.int32, device=DEV)
+    dev = lambda a: torch.from_numpy(np.asarray(a, np.int32)).to(DEV)
+    assert ccl.ccl_spanning(ctx, lat.n, d_lab, None, 0, dev(bot), bot.size, res) == ccl.CCL_OK
+    assert ccl.ccl_sync(ctx) == ccl.CCL_OK and int(res.item()) == -1
+    assert ccl.ccl_spanning(ctx, lat.n, d_lab, dev(top), top.size, None, 0, res) == ccl.CCL_OK
+    assert ccl.ccl_sync(ctx) == ccl.CCL_OK and int(res.item()) == -1
+    bad_top = np.concatenate([[-1, lat.n], top, [lat.n + 5]])
+    bad_bot = np.concatenate([bot, [2 ** 31 - 1]])
+    assert ccl.ccl_spanning(ctx, lat.n, d_lab, dev(bad_top), bad_top.size, dev(bad_bot), bad_bot.size,
+                            res) == ccl.CCL_OK
+    assert ccl.ccl_sync(ctx) == ccl.CCL_ERR_INDEX_OUT_OF_RANGE
+    assert int(res.item()) == want
+    assert np.array_equal(gpu_label(ctx, lat), lab)          # the context is still usable
+
+
 @pytest.mark.parametrize("kind", ["triangle", "honeycomb"])
 def test_spanning(ctx, kind):
     pc = L.PC_TRIANGLE if kind == "triangle" else L.PC_HONEYCOMB

@@ -324,6 +324,48 @@ def test_graph_replay_keyed_on_sizes(ctx):
         assert np.array_equal(out[:lat.n].cpu().numpy(), oracle.uf_label(lat))
 
 
+def test_graph_replay_reads_new_contents():
+    """Same buffers and sizes, new bond bits written in place between calls:
+    the replayed graph labels what the buffers hold now (single and batched)."""
+    c = ccl.ccl_context_create(0)
+    try:
+        _replay_new_contents(c)
+    finally:
+        ccl.ccl_context_destroy(c)
+
+
+def _replay_new_contents(ctx):
+    from ccl_testutil import batch_to_dev
+    lats = [L.triangle(130, p, seed) for p, seed in ((0.30, 1), (0.45, 2), (0.30, 3), (0.60, 4))]
+    rp, ci, bits = to_dev(lats[0])
+    out = torch.empty(lats[0].n, dtype=torch.int32, device=DEV)
+    for k, lat in enumerate(lats):
+        assert np.array_equal(lat.row_ptr, lats[0].row_ptr) and np.array_equal(lat.col_idx, lats[0].col_idx)
+        bits.copy_(torch.from_numpy(lat.open_bits.view(np.int32)).to(DEV))
+        out.fill_(-1)
+        assert ccl.ccl_label(ctx, lat.n, lat.nnz, rp, ci, bits, out) == ccl.CCL_OK
+        assert ccl.ccl_sync(ctx) == ccl.CCL_OK
+        assert np.array_equal(out.cpu().numpy(), oracle.uf_label(lat))
+        if k:
+            assert ccl.ccl_get_stats(ctx).used_graph == 1
+    specs = [dict(kind="honeycomb", L=40, p=0.65, seed=1), dict(kind="cayley", z=3, shells=9, p=0.5, seed=2, perm_seed=2)]
+    b0 = L.make_batch(specs)
+    brp, bci, bbits = batch_to_dev(b0)
+    bout = torch.empty(b0.n_total, dtype=torch.int32, device=DEV)
+    for k, seed in enumerate((5, 6, 7)):
+        b = L.make_batch([dict(sp, seed=seed + i) for i, sp in enumerate(specs)])
+        assert np.array_equal(b.col_idx, b0.col_idx)
+        bbits.copy_(torch.from_numpy(b.open_bits.view(np.int32)).to(DEV))
+        bout.fill_(-1)
+        assert ccl.ccl_label_batched(ctx, b.k, b.site_off, b.ent_off, brp, bci, bbits, bout) == ccl.CCL_OK
+        assert ccl.ccl_sync(ctx) == ccl.CCL_OK
+        got = bout.cpu().numpy()
+        for i in range(b.k):
+            assert np.array_equal(got[int(b.site_off[i]):int(b.site_off[i + 1])], oracle.uf_label(b.instance(i)))
+        if k:
+            assert ccl.ccl_get_stats(ctx).used_graph == 1
+
+
 @pytest.mark.parametrize("refill", [0, 1])
 @pytest.mark.parametrize("order", [0, 1])
 def test_refill_modes_on_uneven_work(refill, order):

@@ -188,3 +188,27 @@ def test_destroy_with_waiters_blocked():
             assert (out == -1).all()
             dropped += 1
     assert dropped >= 1
+
+
+def test_empty_and_edgeless_requests():
+    """Requests with no sites and with sites but no entries, mixed with
+    ordinary ones, copied and not copied."""
+    empty = L.Lattice("e", 0, 0, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(1, np.uint32), 0, 0)
+    isolated = L.Lattice("i", 77, 0, np.zeros(78, np.int32), np.zeros(0, np.int32), np.zeros(1, np.uint32), 0, 0)
+    reqs = [empty, L.triangle(50, L.PC_TRIANGLE, 1), isolated, empty, L.honeycomb(40, L.PC_HONEYCOMB, 2), isolated]
+    srv = ccl.ccl_server_create(0, n_streams=2, max_batch=4)
+    try:
+        tickets = []
+        for k, lat in enumerate(reqs):
+            submit = ccl.ccl_server_submit if k % 2 else ccl.ccl_server_submit_nocopy
+            st, t = submit(srv, lat.n, lat.nnz, lat.row_ptr, lat.col_idx if lat.nnz else lat.row_ptr,
+                           lat.open_bits)
+            assert st == ccl.CCL_OK, ccl.ccl_status_string(st)
+            tickets.append(t)
+        for t, lat in zip(tickets, reqs):
+            out = np.full(max(lat.n, 1), -1, np.int32)
+            st = ccl.ccl_server_wait(srv, t, out, 60_000)
+            assert st == ccl.CCL_OK, ccl.ccl_status_string(st)
+            assert np.array_equal(out[:lat.n], oracle.uf_label(lat))
+    finally:
+        srv.close()
