@@ -69,3 +69,40 @@ def test_binding_names_match_the_abi(lib_path):
     for name in _declared("ccl.h"):
         assert hasattr(ccl, name), name
     assert ccl.LIB_PATH == lib_path
+
+
+def test_binding_structs_and_constants_match_the_header(tmp_path):
+    """Every ctypes struct of the binding has the C struct's size and field
+    offsets, and every CCL_* constant the binding exports has the header's
+    value (a C program built against include/ccl.h prints them)."""
+    import paper_1603_08357_gb300.binding as b
+    structs = [b.ccl_run_stats, b.ccl_server_config, b.ccl_request, b.ccl_server_stats]
+    consts = sorted(n for n in dir(b) if re.fullmatch(r"CCL_[A-Z0-9_]+", n) and isinstance(getattr(b, n), int))
+    assert "CCL_OK" in consts and "CCL_OPT_ANALYSIS_ORDER" in consts
+    lines = ["#include <ccl.h>", "#include <stddef.h>", "#include <stdio.h>", "int main(void) {"]
+    for cls in structs:
+        name = cls.__name__
+        lines.append(f'    printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'    printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    for c in consts:
+        lines.append(f'    printf("const {c} %lld\\n", (long long)({c}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln:
+            *key, val = ln.split(" ")
+            got[" ".join(key)] = int(val)
+    for cls in structs:
+        name = cls.__name__
+        assert got[f"{name} size"] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[f"{name} {field}"] == getattr(cls, field).offset, (name, field)
+    for c in consts:
+        assert got[f"const {c}"] == getattr(b, c), c
