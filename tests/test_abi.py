@@ -79,6 +79,10 @@ def test_binding_structs_and_constants_match_the_header(tmp_path):
     structs = [b.ccl_run_stats, b.ccl_server_config, b.ccl_request, b.ccl_server_stats]
     consts = sorted(n for n in dir(b) if re.fullmatch(r"CCL_[A-Z0-9_]+", n) and isinstance(getattr(b, n), int))
     assert "CCL_OK" in consts and "CCL_OPT_ANALYSIS_ORDER" in consts
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "ccl.h")).read(), flags=re.S)
+    in_header = set(re.findall(r"\b(CCL_[A-Z0-9_]+)\s*=", text))
+    in_header |= set(re.findall(r"#define\s+(CCL_[A-Z0-9_]+)\s+\d+", text))
+    assert in_header and in_header <= set(consts), in_header - set(consts)   # the binding has them all
     lines = ["#include <ccl.h>", "#include <stddef.h>", "#include <stdio.h>", "int main(void) {"]
     for cls in structs:
         name = cls.__name__
@@ -106,3 +110,11 @@ def test_binding_structs_and_constants_match_the_header(tmp_path):
             assert got[f"{name} {field}"] == getattr(cls, field).offset, (name, field)
     for c in consts:
         assert got[f"const {c}"] == getattr(b, c), c
+
+
+def test_binding_has_every_entry_point():
+    """The Python binding offers every C entry point under its C name."""
+    import paper_1603_08357_gb300.binding as b
+    declared = _declared("ccl.h")
+    assert len(declared) >= 20
+    assert [d for d in declared if not callable(getattr(b, d, None))] == []
