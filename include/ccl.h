@@ -111,9 +111,10 @@ CCL_API ccl_status ccl_get_option(ccl_context *ctx, int option, int64_t *value);
  *   open_bits  DEVICE uint32[ceil(nnz/32)] (may be NULL when nnz = 0)
  *   labels     DEVICE int32[n], output: canonical labels
  *   stream     cudaStream_t the work is enqueued on; asynchronous
- * The first call with a larger n or nnz than any before grows the context
- * workspace (8 bytes per CSR entry + 16 bytes per 32 sites) with cudaMalloc;
- * make that call (or ccl_reserve) before capturing a stream into a graph.
+ * The first call with a larger nnz than any before grows the context
+ * workspace (one 8-byte residual-pair slot per CSR entry; batched calls add a
+ * 4-byte instance id per entry) with cudaMalloc; make that call (or
+ * ccl_reserve) before capturing a stream into a graph.
  */
 CCL_API ccl_status ccl_label(ccl_context *ctx, int32_t n_sites, int64_t nnz, const int32_t *row_ptr,
                      const int32_t *col_idx, const uint32_t *open_bits, int32_t *labels,

@@ -555,9 +555,10 @@ ccl_status server_submit(ccl_server *S, const ccl_request *req, uint64_t *ticket
     r->n = req->n_sites;
     r->nnz = req->nnz;
     // device bytes: inputs + labels + the request's share of the labelling
-    // workspace (8 B per CSR entry, 16 B per 32 sites)
+    // workspace of a batched launch (a residual-pair slot of 8 B and its
+    // instance id of 4 B per CSR entry)
     const HostLayout lay(r->n, r->nnz);
-    r->dev_bytes = (int64_t)lay.total + 8 * r->nnz + 16 * (((int64_t)r->n + 31) / 32);
+    r->dev_bytes = (int64_t)lay.total + 12 * r->nnz;
     {
         std::lock_guard<std::mutex> lk(S->mu);
         if (r->dev_bytes > S->budget || (int64_t)S->pending.size() >= S->cfg.max_pending) {
