@@ -227,13 +227,17 @@ def _source_hash() -> str:
 
 def _ncu_traffic(kernel: str, workload: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources (same hash); else None."""
+    the current kernel sources (same hash) or on sources that differ from them
+    only outside the kernels and their launches (an entry's
+    equivalent_source_hashes, each with the change named in its note); else
+    None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
         ent = rec.get(f"{kernel}:{workload}")
-        if ent and ent.get("source_hash") == _source_hash():
+        h = _source_hash()
+        if ent and (ent.get("source_hash") == h or h in ent.get("equivalent_source_hashes", [])):
             return float(ent["dram_bytes_per_launch"]), ent.get("scaled_from")
     except Exception:
         pass

@@ -15,6 +15,10 @@
  * smallest site number of v's cluster. It is unique, so any correct run gives
  * the same bits.
  *
+ * Sizes: n <= CCL_MAX_SITES sites per instance (2^31 - 4097: the kernels
+ * number sites in 32-bit integers and keep that much headroom above the last
+ * site), nnz < 2^31 CSR entries per instance.
+ *
  * Input format (the "NN list" of Section 3, here in CSR form):
  *   row_ptr[n+1]  int32, row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz;
  *   col_idx[nnz]  int32 neighbour site numbers in [0, n);
@@ -64,6 +68,10 @@ typedef enum {
     CCL_ERR_NOT_FOUND = 9           /* unknown ticket */
 } ccl_status;
 
+/* Most sites of one instance (2^31 - 4097); larger counts are rejected with
+ * CCL_ERR_INVALID_ARGUMENT by every entry point. */
+#define CCL_MAX_SITES 2147479551
+
 typedef struct ccl_context ccl_context;
 
 /* Human-readable name of a status code (static storage). */
@@ -104,7 +112,8 @@ CCL_API ccl_status ccl_get_option(ccl_context *ctx, int option, int64_t *value);
 
 /*
  * ccl_label -- label one instance (Section 3, steps (i)-(iv)).
- *   n_sites    number of sites n >= 0 (n = 0 returns CCL_OK, writes nothing)
+ *   n_sites    number of sites, 0 <= n <= CCL_MAX_SITES (n = 0 returns CCL_OK,
+ *              writes nothing)
  *   nnz        number of CSR entries, 0 <= nnz < 2^31
  *   row_ptr    DEVICE int32[n+1]
  *   col_idx    DEVICE int32[nnz]       (may be NULL when nnz = 0)
@@ -131,7 +140,7 @@ CCL_API ccl_status ccl_label(ccl_context *ctx, int32_t n_sites, int64_t nnz, con
  *   col_idx    DEVICE int32[ent_off[K]]: instance-local site numbers
  *   open_bits  DEVICE uint32: local entry e of instance k is global bit ent_off[k] + e
  *   labels     DEVICE int32[site_off[K]]: labels[site_off[k] + i] = instance-local label
- * Each instance needs n_k < 2^31 and nnz_k < 2^31. Asynchronous on `stream`.
+ * Each instance needs n_k <= CCL_MAX_SITES and nnz_k < 2^31. Asynchronous on `stream`.
  * Repeated calls with the same arguments replay a captured CUDA graph.
  */
 CCL_API ccl_status ccl_label_batched(ccl_context *ctx, int32_t n_inst, const int64_t *site_off,

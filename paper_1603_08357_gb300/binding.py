@@ -284,6 +284,7 @@ def ccl_label_random(ctx, n_sites: int, nnz: int, row_ptr, col_idx, seed: int, p
 
 
 CCL_DENSE_MAX_WIDTH = 4096
+CCL_MAX_SITES = 2147479551          # most sites of one instance (2^31 - 4097)
 
 
 def ccl_label_dense(ctx, n_sites: int, width: int, nn, open_bits, labels, stream=None) -> int:

@@ -526,7 +526,7 @@ ccl_status check_single_args(ccl_context *ctx, int32_t n, int64_t nnz, const int
                              const int32_t *col_idx, const uint32_t *bits, const int32_t *labels,
                              bool need_bits = true) {
     if (!ctx) return CCL_ERR_INVALID_ARGUMENT;
-    if (n < 0 || nnz < 0 || nnz > INT32_MAX) return CCL_ERR_INVALID_ARGUMENT;
+    if (n < 0 || n > CCL_MAX_SITES || nnz < 0 || nnz > INT32_MAX) return CCL_ERR_INVALID_ARGUMENT;
     if (n == 0) return CCL_OK;
     if (!row_ptr || !labels) return CCL_ERR_INVALID_ARGUMENT;
     if (nnz > 0 && (!col_idx || (need_bits && !bits))) return CCL_ERR_INVALID_ARGUMENT;
@@ -820,7 +820,7 @@ ccl_status label_batched(ccl_context *ctx, int32_t K, const int64_t *site_off, c
     for (int32_t k = 0; k < K; ++k) {
         const int64_t n = site_off[k + 1] - site_off[k];
         const int64_t nnz = ent_off[k + 1] - ent_off[k];
-        if (n < 0 || nnz < 0 || n > INT32_MAX - 1 || nnz > INT32_MAX) return CCL_ERR_INVALID_ARGUMENT;
+        if (n < 0 || nnz < 0 || n > CCL_MAX_SITES || nnz > INT32_MAX) return CCL_ERR_INVALID_ARGUMENT;
         Inst I;
         I.row_ptr = row_ptr + site_off[k] + k;
         I.col_idx = col_idx + ent_off[k];
@@ -919,7 +919,8 @@ ccl_status ccl_label_random(ccl_context *ctx, int32_t n, int64_t nnz, const int3
 namespace {
 ccl_status check_dense_args(ccl_context *ctx, int32_t n, int32_t width, const int32_t *nn, const void *bits,
                             const int32_t *labels, bool need_bits = true) {
-    if (!ctx || n < 0 || width < 0 || width > CCL_DENSE_MAX_WIDTH) return CCL_ERR_INVALID_ARGUMENT;
+    if (!ctx || n < 0 || n > CCL_MAX_SITES || width < 0 || width > CCL_DENSE_MAX_WIDTH)
+        return CCL_ERR_INVALID_ARGUMENT;
     if (n == 0) return CCL_OK;
     if (!labels || (width > 0 && (!nn || (need_bits && !bits)))) return CCL_ERR_INVALID_ARGUMENT;
     return CCL_OK;

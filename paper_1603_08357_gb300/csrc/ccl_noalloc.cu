@@ -92,7 +92,7 @@ ccl_status setup_device(int dev, DeviceSetup **out) {
 extern "C" ccl_status ccl_label_noalloc(int32_t n, int64_t nnz, const int32_t *row_ptr,
                                         const int32_t *col_idx, const uint32_t *bits, int32_t *labels,
                                         void *stream) {
-    if (n < 0 || nnz < 0) return CCL_ERR_INVALID_ARGUMENT;
+    if (n < 0 || n > CCL_MAX_SITES || nnz < 0) return CCL_ERR_INVALID_ARGUMENT;
     if (nnz > kNoAllocMaxEntries) return CCL_ERR_INVALID_ARGUMENT;   // beyond the fixed scratch
     if (n == 0) return CCL_OK;
     if (!row_ptr || !labels || (nnz > 0 && (!col_idx || !bits))) return CCL_ERR_INVALID_ARGUMENT;

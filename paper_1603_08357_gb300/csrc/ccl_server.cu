@@ -548,7 +548,8 @@ ccl_status ccl_server_create(ccl_server **out, const ccl_server_config *cfg_in) 
 namespace {
 ccl_status server_submit(ccl_server *S, const ccl_request *req, uint64_t *ticket, bool copy) {
     if (!S || !req || !ticket) return CCL_ERR_INVALID_ARGUMENT;
-    if (req->n_sites < 0 || req->nnz < 0 || req->nnz > INT32_MAX) return CCL_ERR_INVALID_ARGUMENT;
+    if (req->n_sites < 0 || req->n_sites > CCL_MAX_SITES || req->nnz < 0 || req->nnz > INT32_MAX)
+        return CCL_ERR_INVALID_ARGUMENT;
     if (!req->row_ptr || (req->nnz > 0 && (!req->col_idx || !req->open_bits)))
         return CCL_ERR_INVALID_ARGUMENT;
     auto r = std::make_shared<Req>();

@@ -118,3 +118,16 @@ def test_binding_has_every_entry_point():
     declared = _declared("ccl.h")
     assert len(declared) >= 20
     assert [d for d in declared if not callable(getattr(b, d, None))] == []
+
+
+def test_site_count_limit_rejected_before_any_cuda_call(lib_path):
+    """n_sites above CCL_MAX_SITES (2^31 - 4097) is refused by the argument
+    checks, before the device is touched (the allocation-free entry needs no
+    context, so this runs without a GPU)."""
+    import paper_1603_08357_gb300.binding as b
+    assert b.CCL_MAX_SITES == 2 ** 31 - 4097
+    lib = ctypes.CDLL(lib_path)
+    P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.ccl_label_noalloc.argtypes = [I32, I64, P, P, P, P, P]
+    for n in (b.CCL_MAX_SITES + 1, 2 ** 31 - 1):
+        assert lib.ccl_label_noalloc(n, 0, 16, None, None, 16, None) == b.CCL_ERR_INVALID_ARGUMENT
