@@ -354,8 +354,8 @@ def run_ours(args, rank, world, local):
         step()
     ccl.check(ccl.ccl_sync(ctx, stream), "warm-up")
 
-    # correctness guard: the timed labels are compared with the oracle on a
-    # sample of sites (every rank, its own instance) -- full comparison in tests
+    # correctness guard: the CPU-baseline leg compares every label of the last
+    # timed step with the oracle's labels of the same instance (rank 0, N=1)
     stats = ccl.ccl_get_stats(ctx)
     q = int(stats.residual_pairs)
 

@@ -214,11 +214,17 @@ CCL_API ccl_status ccl_label_host(ccl_context *ctx, int32_t n_sites, int64_t nnz
  *   (device pointers owned by the caller, work on `stream`).
  * Limit: nnz <= 2,097,152 CSR entries; larger inputs return
  * CCL_ERR_INVALID_ARGUMENT without touching the device.
- * Synchronous: waits for `stream`, then returns the kernels' status
+ * Synchronous: enqueues the kernels and the read of the status word on
+ * `stream`, waits for `stream` alone, then returns the kernels' status
  * (CCL_OK, CCL_ERR_INDEX_OUT_OF_RANGE, CCL_ERR_INVALID_ARGUMENT,
  * CCL_ERR_NONCONVERGED) or CCL_ERR_CUDA.
  * The first call on a device takes the array's device address and sets up
  * the kernels for that device; make that first call before any stream capture.
+ * With CUDA's lazy module loading (the default since CUDA 12.2) the array
+ * itself comes into being during that first call, when the library's device
+ * code is loaded, so the first call can still fail (CCL_ERR_OUT_OF_MEMORY or
+ * CCL_ERR_CUDA) if the device is full: make it at start-up. Later calls
+ * allocate nothing.
  * All calls share the one array, so calls that overlap on the GPU (other
  * streams, other host threads) race; serialise them.
  */
@@ -290,6 +296,8 @@ typedef struct {
     int64_t chase_loads, merge_atomics, reduce_iterations;
 } ccl_run_stats;
 
+/* Statistics of the context's last labelling call; waits for that call to
+ * finish (not for other work on the device). */
 CCL_API ccl_status ccl_get_stats(ccl_context *ctx, ccl_run_stats *stats);
 
 /* Per-step device times (ms), averaged over the calls made since
@@ -339,6 +347,20 @@ CCL_API ccl_status ccl_autotune_batched(ccl_context *ctx, int32_t n_inst, const 
  * memory of its own, gathers every uploaded request into one batched launch
  * per tick on one of n_streams compute streams, so later arrivals are labelled
  * while earlier batches are still on the GPU, and copies labels back.
+ *
+ * Memory counted against the budget: each admitted request's device buffer
+ * (inputs and labels, 4(n+1) + 4 nnz + 4 ceil(nnz/32) + 4n bytes, each part
+ * rounded up to 256) and, until its batch is launched, 12 bytes per CSR entry
+ * for its share of the batched workspace; plus the workspace every compute
+ * stream's context keeps after its largest batch. When only that kept
+ * workspace stands in the way of the next request, idle contexts free it.
+ * A request whose buffer cannot be allocated (other programs hold the memory)
+ * while the server holds nothing for other requests ends after 2 s with
+ * CCL_ERR_OUT_OF_MEMORY. A batch whose launch fails ends each of its
+ * requests with that error.
+ * Test hook: the environment variable CCL_SERVER_FAIL_BATCH=k, read by
+ * ccl_server_create, makes the k-th batch launch of that server fail with
+ * CCL_ERR_OUT_OF_MEMORY without running (as a failed workspace allocation).
  * ------------------------------------------------------------------------- */
 
 typedef struct ccl_server ccl_server;

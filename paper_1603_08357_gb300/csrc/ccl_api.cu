@@ -71,6 +71,9 @@ struct ccl_context {
     Inst *h_insts = nullptr;     // pinned staging
     int64_t h_insts_cap = 0;
     cudaEvent_t staging_free = nullptr;
+    // recorded after each labelling call (outside stream capture): statistics
+    // reads wait for it instead of the whole device
+    cudaEvent_t stats_ev = nullptr;
     // host-buffer path: device copies of the inputs, and the copy stream and
     // events that overlap the upload of later parts with step (i) on earlier ones
     void *d_host_in = nullptr;
@@ -456,6 +459,7 @@ ccl_status run(ccl_context *ctx, Params P, bool batched, const TuneChoice &tc, c
         }
         ccl_status st = enqueue_steps(ctx, P, batched, tc, s, ctx->profile != 0);
         if (st == CCL_OK && ctx->profile) { ctx->have_times = 1; ctx->prof_count++; }
+        if (st == CCL_OK && !capturing) CCL_CUDA(cudaEventRecord(ctx->stats_ev, s));
         return st;
     }
     GraphEntry key;
@@ -490,6 +494,7 @@ ccl_status run(ccl_context *ctx, Params P, bool batched, const TuneChoice &tc, c
     }
     g->last_use = ++ctx->use_clock;
     CCL_CUDA(cudaGraphLaunch(g->exec, s));
+    CCL_CUDA(cudaEventRecord(ctx->stats_ev, s));
     ctx->last.used_graph = 1;
     return CCL_OK;
 }
@@ -635,6 +640,26 @@ ccl_status label_instances(ccl_context *ctx, std::vector<Inst> &table, cudaStrea
     return run(ctx, P, true, tc, s, &table, 0, false);
 }
 
+// Device bytes the context's residual-pair workspace holds now (it grows with
+// the largest call and is kept until released).
+int64_t workspace_bytes(const ccl_context *ctx) {
+    return ctx->q_cap * (int64_t)sizeof(int2) + ctx->qk_cap * (int64_t)sizeof(int32_t);
+}
+
+// Frees the residual-pair workspace (and the graphs that point into it); the
+// next call allocates it again. The caller makes sure no work of the context
+// is still running.
+void release_workspace(ccl_context *ctx) {
+    DeviceGuard guard(ctx->device);
+    drop_graphs(ctx);
+    if (ctx->d_q) cudaFree(ctx->d_q);
+    if (ctx->d_qk) cudaFree(ctx->d_qk);
+    ctx->d_q = nullptr;
+    ctx->d_qk = nullptr;
+    ctx->q_cap = ctx->qk_cap = 0;
+    (void)cudaGetLastError();
+}
+
 }  // namespace ccl
 
 extern "C" {
@@ -675,6 +700,7 @@ ccl_status ccl_context_create(ccl_context **out, int device) {
     if (e == cudaSuccess) e = cudaMemset(ctx->d_counters, 0, 4 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->staging_free, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->stats_ev, cudaEventDisableTiming);
     // the opt-in shared memory of the staging buffers
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_init<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -734,6 +760,7 @@ void ccl_context_destroy(ccl_context *ctx) {
     for (auto &e : ctx->part_ev) if (e) cudaEventDestroy(e);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->staging_free) cudaEventDestroy(ctx->staging_free);
+    if (ctx->stats_ev) cudaEventDestroy(ctx->stats_ev);
     for (auto &set : ctx->prof)
         for (auto &e : set) if (e) cudaEventDestroy(e);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -1104,7 +1131,9 @@ ccl_status label_host_parts(ccl_context *ctx, int32_t n, int64_t nnz, const int3
     P.n_tiles = tiles;
     P.band_off = 0;
     P.n_bands = band_off;
-    return enqueue_tail(ctx, P, false, tc, s, false);
+    st = enqueue_tail(ctx, P, false, tc, s, false);
+    if (st == CCL_OK) CCL_CUDA(cudaEventRecord(ctx->stats_ev, s));
+    return st;
 }
 }  // namespace
 
@@ -1171,9 +1200,11 @@ ccl_status ccl_validate(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t 
 ccl_status ccl_get_stats(ccl_context *ctx, ccl_run_stats *out) {
     if (!ctx || !out) return CCL_ERR_INVALID_ARGUMENT;
     DeviceGuard guard(ctx->device);
-    CCL_CUDA(cudaDeviceSynchronize());
+    CCL_CUDA(cudaEventSynchronize(ctx->stats_ev));    // the last labelling call has finished
     unsigned long long c[4] = {0, 0, 0, 0};
-    CCL_CUDA(cudaMemcpy(c, ctx->d_counters, sizeof(c), cudaMemcpyDeviceToHost));
+    // read on the context's own non-blocking stream: no wait on other streams
+    CCL_CUDA(cudaMemcpyAsync(c, ctx->d_counters, sizeof(c), cudaMemcpyDeviceToHost, ctx->cap_stream));
+    CCL_CUDA(cudaStreamSynchronize(ctx->cap_stream));
     *out = ctx->last;
     out->residual_pairs = (int64_t)c[0];
     out->chase_loads = (int64_t)c[1];

@@ -153,9 +153,12 @@ extern "C" ccl_status ccl_label_noalloc(int32_t n, int64_t nnz, const int32_t *r
         k_analysis<false, true><<<(unsigned)g_ana, 256, 0, s>>>(P);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    // the error word comes back on the call's own stream (no wait on other
+    // streams of the device), then the call waits for that stream
     unsigned err = 0;
-    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&err, g_noalloc_scratch, sizeof(unsigned), kOffErr);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&err, d->scratch + kOffErr, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return CCL_ERR_CUDA;

@@ -37,12 +37,17 @@
 
 namespace ccl {
 ccl_status label_instances(ccl_context *ctx, std::vector<Inst> &table, cudaStream_t s);
+int64_t workspace_bytes(const ccl_context *ctx);
+void release_workspace(ccl_context *ctx);
 }
 
 namespace {
 
 using Clock = std::chrono::steady_clock;
 constexpr int kUploaders = 2;    // uploader threads, each with a stream of its own
+// a request whose device buffer cannot be allocated although the server holds
+// nothing for other requests fails with CCL_ERR_OUT_OF_MEMORY after this long
+constexpr auto kAllocGiveUp = std::chrono::milliseconds(2000);
 
 struct Req {
     uint64_t ticket = 0;
@@ -60,7 +65,10 @@ struct Req {
     size_t lab_bytes = 0;
     std::vector<int32_t> v_row_ptr, v_col_idx, v_labels;
     std::vector<uint32_t> v_bits;
-    int64_t dev_bytes = 0;
+    int64_t dev_bytes = 0;      // its device buffer: inputs and labels
+    int64_t ws_bytes = 0;       // its share of a batched launch's workspace (until launched)
+    bool alloc_failing = false; // the pool could not allocate its buffer ...
+    Clock::time_point t_alloc_fail;  // ... since then
     char *d_mem = nullptr;
     cudaEvent_t uploaded = nullptr;
     Clock::time_point t_submit, t_done;
@@ -211,7 +219,15 @@ struct HostArena {
 struct ccl_server {
     ccl_server_config cfg{};
     int64_t budget = 0;
+    // Device bytes counted against the budget: every admitted request's buffer
+    // (held_req) and, until it is launched, its workspace share; plus the
+    // workspace each context keeps after its largest batch (ws_slot).
     int64_t held = 0;
+    int64_t held_req = 0;
+    std::vector<int64_t> ws_slot;
+    bool trim_ws = false;       // the uploader asks the server thread to free idle workspaces
+    int64_t launches = 0;
+    int64_t fail_batch = 0;     // test hook (CCL_SERVER_FAIL_BATCH): this launch fails, 0 = none
     std::vector<ccl_context *> ctxs;
     std::vector<cudaStream_t> streams;
     std::vector<bool> slot_busy;
@@ -270,10 +286,11 @@ void retire(ccl_server *S, Batch &b) {
     S->slot_busy[(size_t)b.slot] = false;
     std::lock_guard<std::mutex> lk(S->mu);
     for (auto &r : b.reqs) {
-        r->status = st;
+        if (r->status == CCL_OK) r->status = st;    // an error from the launch stays
         r->t_done = now;
         r->done = true;
         S->held -= r->dev_bytes;
+        S->held_req -= r->dev_bytes;
         S->completed++;
         S->sites_completed += r->n;
         S->lat_ms.push_back(std::chrono::duration<double, std::milli>(now - r->t_submit).count());
@@ -335,7 +352,30 @@ void launch_batch(ccl_server *S, int slot, std::vector<std::shared_ptr<Req>> req
         I.nnz = (int32_t)r->nnz;
         table.push_back(I);
     }
-    ccl_status st = ccl::label_instances(S->ctxs[(size_t)slot], table, s);
+    ccl_context *ctx = S->ctxs[(size_t)slot];
+    const int64_t ws_before = ccl::workspace_bytes(ctx);
+    ccl_status st = CCL_OK;
+    if (S->fail_batch > 0 && ++S->launches == S->fail_batch) {
+        st = CCL_ERR_OUT_OF_MEMORY;     // test hook: as if the workspace could not be allocated
+    } else {
+        st = ccl::label_instances(ctx, table, s);
+        if (st == CCL_ERR_OUT_OF_MEMORY) {
+            // the pool may keep freed request buffers that the workspace's
+            // cudaMalloc cannot use: hand them back and try once more
+            cudaMemPoolTrimTo(S->pool, 0);
+            (void)cudaGetLastError();
+            st = ccl::label_instances(ctx, table, s);
+        }
+    }
+    {
+        // the batch's workspace shares are released; the context now keeps
+        // ws_after bytes of workspace (at most the shares it was granted)
+        const int64_t ws_after = ccl::workspace_bytes(ctx);
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (auto &r : reqs) { S->held -= r->ws_bytes; r->ws_bytes = 0; }
+        S->held += ws_after - ws_before;
+        S->ws_slot[(size_t)slot] = ws_after;
+    }
     for (size_t t = 0; t < reqs.size(); ++t) {
         auto &r = reqs[t];
         if (pinned_labels(*r) && r->n > 0)
@@ -366,6 +406,24 @@ void server_loop(ccl_server *S) {
                 if (e != cudaSuccess) { (void)cudaGetLastError(); r->status = CCL_ERR_CUDA; }
                 S->ready.push_back(r);
                 S->uploading.pop_front();
+                progressed = true;
+            }
+        }
+        // 2. free the workspace idle contexts keep, when it blocks admission
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            if (S->trim_ws) {
+                S->trim_ws = false;
+                for (size_t slot = 0; slot < S->ctxs.size(); ++slot) {
+                    if (S->slot_busy[slot] || S->ws_slot[slot] == 0) continue;
+                    const int64_t ws = S->ws_slot[slot];
+                    lk.unlock();
+                    ccl::release_workspace(S->ctxs[slot]);
+                    lk.lock();
+                    S->held -= ws;
+                    S->ws_slot[slot] = 0;
+                }
+                S->cv_upload.notify_all();
                 progressed = true;
             }
         }
@@ -433,21 +491,42 @@ void upload_loop(ccl_server *S, cudaStream_t up) {
             continue;
         }
         auto r = S->pending.front();
-        if (S->held + r->dev_bytes > S->budget && S->held > 0) {   // wait for memory to free up
+        if (S->held + r->dev_bytes + r->ws_bytes > S->budget && S->held > 0) {
+            // wait for memory to free up; if only the workspace kept by idle
+            // contexts stands in the way, ask the server thread to free it
+            if (S->held_req == 0) { S->trim_ws = true; S->cv_work.notify_one(); }
             S->cv_upload.wait_for(lk, std::chrono::microseconds(200));
             continue;
         }
         S->pending.pop_front();
-        S->held += r->dev_bytes;
+        S->held += r->dev_bytes + r->ws_bytes;
+        S->held_req += r->dev_bytes;
         lk.unlock();
         const bool ok = start_upload(S, r, up);
         lk.lock();
-        if (!ok) {     // pool full right now: retry later
-            S->held -= r->dev_bytes;
+        if (!ok) {
+            // the pool cannot allocate right now (other work holds the
+            // memory): retry later; once the server holds nothing for other
+            // requests and this has lasted kAllocGiveUp, the request fails
+            S->held -= r->dev_bytes + r->ws_bytes;
+            S->held_req -= r->dev_bytes;
+            const auto now = Clock::now();
+            if (!r->alloc_failing) { r->alloc_failing = true; r->t_alloc_fail = now; }
+            const bool alone = S->held_req == 0;
+            if (alone && now - r->t_alloc_fail > kAllocGiveUp) {
+                r->status = CCL_ERR_OUT_OF_MEMORY;
+                r->t_done = now;
+                r->done = true;
+                S->completed++;
+                S->cv_done.notify_all();
+                continue;
+            }
+            if (alone) { S->trim_ws = true; S->cv_work.notify_one(); }
             S->pending.push_front(r);
             S->cv_upload.wait_for(lk, std::chrono::microseconds(200));
             continue;
         }
+        r->alloc_failing = false;
         S->uploading.push_back(r);
         S->cv_work.notify_one();
     }
@@ -529,6 +608,10 @@ ccl_status ccl_server_create(ccl_server **out, const ccl_server_config *cfg_in) 
         return CCL_ERR_CUDA;
     }
     S->slot_busy.assign(S->streams.size(), false);
+    S->ws_slot.assign(S->streams.size(), 0);
+    // test hook: CCL_SERVER_FAIL_BATCH=k makes the k-th batch launch report
+    // CCL_ERR_OUT_OF_MEMORY without running, as a failed workspace allocation would
+    if (const char *env = getenv("CCL_SERVER_FAIL_BATCH")) S->fail_batch = std::max(0, atoi(env));
     {
         // copy threads: CCL_SERVER_COPY_THREADS, else three quarters of the host's cores, at most 12
         const unsigned hw = std::max(2u, std::thread::hardware_concurrency());
@@ -559,10 +642,11 @@ ccl_status server_submit(ccl_server *S, const ccl_request *req, uint64_t *ticket
     // workspace of a batched launch (a residual-pair slot of 8 B and its
     // instance id of 4 B per CSR entry)
     const HostLayout lay(r->n, r->nnz);
-    r->dev_bytes = (int64_t)lay.total + 12 * r->nnz;
+    r->dev_bytes = (int64_t)lay.total;
+    r->ws_bytes = 12 * r->nnz;
     {
         std::lock_guard<std::mutex> lk(S->mu);
-        if (r->dev_bytes > S->budget || (int64_t)S->pending.size() >= S->cfg.max_pending) {
+        if (r->dev_bytes + r->ws_bytes > S->budget || (int64_t)S->pending.size() >= S->cfg.max_pending) {
             S->rejected++;
             return CCL_ERR_REJECTED;
         }

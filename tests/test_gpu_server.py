@@ -212,3 +212,39 @@ def test_empty_and_edgeless_requests():
             assert np.array_equal(out[:lat.n], oracle.uf_label(lat))
     finally:
         srv.close()
+
+
+def test_failed_batch_launch_is_reported(monkeypatch):
+    """A batch whose launch fails (here its first launch, made to fail by the
+    server's test hook as a failed workspace allocation would) ends its
+    request with that error, not with CCL_OK and unwritten labels; the server
+    then labels the next request correctly."""
+    monkeypatch.setenv("CCL_SERVER_FAIL_BATCH", "1")
+    srv = ccl.ccl_server_create(0, n_streams=1, max_batch=8)
+    monkeypatch.delenv("CCL_SERVER_FAIL_BATCH")
+    try:
+        lat = L.triangle(64, L.PC_TRIANGLE, 5)
+        out = np.full(lat.n, -1, np.int32)
+        st = ccl.ccl_server_wait(srv, _submit(srv, lat), out, 60_000)
+        assert st == ccl.CCL_ERR_OUT_OF_MEMORY, ccl.ccl_status_string(st)
+        assert np.array_equal(_wait(srv, _submit(srv, lat), lat.n), oracle.uf_label(lat))
+    finally:
+        ccl.ccl_server_destroy(srv)
+
+
+def test_kept_workspace_is_counted_and_freed():
+    """The workspace a context keeps after a large batch counts against the
+    budget; when it alone blocks the next request, the idle context frees it
+    and the request is labelled (a budget that fits one large request's
+    buffer and workspace share, but not that plus the workspace kept from the
+    previous batch)."""
+    big = L.triangle(1024, L.PC_TRIANGLE, 6)
+    nnz = big.nnz
+    per_req = 4 * (big.n + 1) + 4 * nnz + 4 * ((nnz + 31) // 32) + 4 * big.n + 4 * 256 + 12 * nnz
+    srv = ccl.ccl_server_create(0, n_streams=2, max_batch=1, hbm_budget=int(per_req * 1.2))
+    try:
+        want = oracle.uf_label(big)
+        for _ in range(4):      # each request after the first needs the kept workspace freed
+            assert np.array_equal(_wait(srv, _submit(srv, big), big.n), want)
+    finally:
+        ccl.ccl_server_destroy(srv)

@@ -40,6 +40,24 @@ def test_noalloc_matches_ccl_label_twice(ctx):
         assert np.array_equal(first, oracle.uf_label(lat))
 
 
+def test_noalloc_allocates_nothing_after_the_first_call():
+    """After the first call on the device (which loads the library's device
+    code and with it the fixed array), further calls leave the device's free
+    memory unchanged: every buffer here exists before the calls."""
+    lat = L.triangle(700, L.PC_TRIANGLE, 8)
+    rp, ci, bits = to_dev(lat)
+    out = torch.full((lat.n,), -5, dtype=torch.int32, device=DEV)
+    assert ccl.ccl_label_noalloc(lat.n, lat.nnz, rp, ci, bits, out) == ccl.CCL_OK
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        out.fill_(-5)
+        assert ccl.ccl_label_noalloc(lat.n, lat.nnz, rp, ci, bits, out) == ccl.CCL_OK
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+    assert np.array_equal(out.cpu().numpy(), oracle.uf_label(lat))
+
+
 def test_noalloc_at_its_limit():
     """Exactly 2^21 CSR entries (the largest input its scratch holds): the
     oracle's labels."""
