@@ -47,6 +47,7 @@ CONFIGS = {
                      desc="triangle bond percolation 16384x16384 periodic p=0.3473"),
 }
 L2_BYTES = 129 * 1024 * 1024
+METRIC = "sites labeled/s per GB300 (batched vs one-at-a-time); achieved HBM GB/s"
 
 
 def _env_rank():
@@ -187,10 +188,12 @@ def max_over_ranks(value: float, dist, device=None) -> float:
     return float(t.item())
 
 
-def algorithmic_bytes(n: int, nnz: int, q: int, input_kind: str = "csr", width: int = 0) -> dict:
+def algorithmic_bytes(n: int, nnz: int, q: int, input_kind: str = "csr", width: int = 0,
+                      rows: int | None = None) -> dict:
     """Minimum bytes each step must move (each array read or written once).
 
-    init (csr):          row_ptr 4(n+1) + col_idx 4 nnz + bit words 4 ceil(nnz/32)
+    init (csr):          row_ptr 4 rows (n+1, or n+K for K batched instances)
+                         + col_idx 4 nnz + bit words 4 ceil(nnz/32)
                          + labels 4n + residual pairs 8q
     init (random):       as csr without the bit words (bonds drawn on the device)
     init (dense):        neighbour slots 4 width n + bit words 4 ceil(width n/32)
@@ -203,7 +206,8 @@ def algorithmic_bytes(n: int, nnz: int, q: int, input_kind: str = "csr", width: 
         slots = width * n
         b_in = 4 * slots + (4 * ((slots + 31) // 32) if input_kind == "dense" else 0)
     else:
-        b_in = 4 * (n + 1) + 4 * nnz + (4 * ((nnz + 31) // 32) if input_kind == "csr" else 0)
+        b_in = 4 * (n + 1 if rows is None else rows) + 4 * nnz + \
+            (4 * ((nnz + 31) // 32) if input_kind == "csr" else 0)
     b_init = b_in + 4 * n + 8 * q
     b_ana = 8 * n
     b_red = 16 * q
@@ -246,56 +250,54 @@ def _ncu_traffic(kernel: str, workload: str):
 
 # ----------------------------------------------------------------------------
 
-def _reference_sample(config: str):
-    """The instances one reference step labels: the whole instance for the
-    single-instance configs; for the batched and served mixes a bounded
-    sample of their instances (the first ones of the seeded stream)."""
-    if config == "batched":
-        specs = L.batched_mix_specs(4096, seed=4)[:24]
-        return [L.make_instance(sp) for sp in specs], "batched mix, first 24 instances"
-    if config == "served":
-        specs = L.served_specs(2000, seed=5)[:24]
-        return [L.make_instance(sp) for sp in specs], "served stream, first 24 requests"
-    lat, desc = make_workload(config, 0)
-    return [lat], desc
+def _reference_sample(args):
+    """What one reference step labels, as (run_step, sites, entries, desc,
+    cores): the whole instance (one core) for the single-instance configs;
+    for the batched mix its first --reference-instances instances with whole
+    instances spread over the host's cores (as the CPU-baseline leg does);
+    for the served stream its first 24 requests (one core)."""
+    import oracle
+    if args.config == "batched":
+        specs = L.batched_mix_specs(args.instances, seed=4)[:args.reference_instances]
+        sb = L.make_batch(specs)
+        cores = os.cpu_count() or 1
+        return (lambda: oracle.uf_label_batched_threads(sb, cores), sb.n_total, sb.nnz_total,
+                f"batched mix, first {sb.k} instances, whole instances over {cores} threads", cores)
+    if args.config == "served":
+        lats = [L.make_instance(sp) for sp in L.served_specs(args.requests, seed=5)[:24]]
+        desc = "served stream, first 24 requests"
+    else:
+        lats, desc = [make_workload(args.config, 0)[0]], make_workload(args.config, 0)[1]
+
+    def run_step():
+        for x in lats:
+            oracle.uf_label(x)
+    return run_step, sum(x.n for x in lats), sum(x.nnz for x in lats), desc, 1
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    lats, desc = _reference_sample(args.config)
-    lat = lats[0]
-    import oracle
-    n_step = sum(x.n for x in lats)
-
-    def one_step():
-        for x in lats:
-            oracle.uf_label(x)
-
-    per_step = []
+    one_step, n_step, nnz_step, desc, cores = _reference_sample(args)
     for _ in range(args.warmup):
         one_step()
     t_all = time.perf_counter()
     for _ in range(args.steps):
-        t0 = time.perf_counter()
         one_step()
-        per_step.append(time.perf_counter() - t0)
     wall = time.perf_counter() - t_all
     ms = 1e3 * wall / args.steps
     value = n_step / (ms / 1e3)
     line = {
         "impl": "reference", "value": value, "unit": "sites/s",
-        "metric": {"batched": "sites labeled/s (batched)", "served": "sites labeled/s (served)"}.get(
-            args.config, "sites labeled/s"),
+        "metric": METRIC if args.config == "batched" else (
+            "sites labeled/s (served)" if args.config == "served" else "sites labeled/s"),
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": args.config, "desc": desc, "n_sites": n_step,
-                   "nnz": sum(x.nnz for x in lats),
-                   "l2": "inputs larger than L2 (no flush)" if lat.nnz * 4 > L2_BYTES else "L2-resident"},
-        "cpu_baseline": {"value": value, "unit": "sites/s", "cores": 1, "kind": "oracle",
-                         "sample": f"union-find oracle over {desc} ({n_step} sites), "
-                                   f"one pass per step, 1 thread"},
+        "config": {"workload": args.config, "desc": desc, "n_sites": n_step, "nnz": nnz_step,
+                   "l2": "inputs larger than L2 (no flush)" if nnz_step * 4 > L2_BYTES else "L2-resident"},
+        "cpu_baseline": {"value": value, "unit": "sites/s", "cores": cores, "kind": "oracle",
+                         "sample": f"union-find oracle over {desc} ({n_step} sites), one pass per step"},
         "e2e": {"value": value, "unit": "sites/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -504,10 +506,39 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def _pin(arrays):
+    """Page-locks host numpy arrays in place (cudaHostRegister through
+    torch's runtime binding) so that copies from and to them run at the
+    host link's full rate; returns an undo function."""
+    import torch
+    rt = torch.cuda.cudart()
+    done = []
+    for a in arrays:
+        if a.nbytes == 0:
+            continue
+        if int(rt.cudaHostRegister(a.ctypes.data, a.nbytes, 0)) != 0:
+            raise RuntimeError("cudaHostRegister failed")
+        done.append(a)
+
+    def undo():
+        for a in done:
+            rt.cudaHostUnregister(a.ctypes.data)
+    return undo
+
+
 def run_batched(args, rank, world, local):
-    """The batched workload: K mixed instances labelled by one pass of the four
-    steps (ccl_label_batched, graph replay), against the same instances
-    labelled one ccl_label call at a time."""
+    """The batched workload (the metric's headline): K mixed instances labelled
+    by one pass of the four steps (ccl_label_batched), against the same
+    instances labelled one ccl_label call at a time, both in this run.
+
+    value: batched sites/s from per-step CUDA events, inputs resident in HBM.
+    roofline: the dominant kernel of the batched step (per-kernel events of
+    the same timed steps) against the measured copy bandwidth.
+    e2e: ccl_label_batched_host from page-locked host arrays (inputs up,
+    labels down, inside the timed region).
+    cpu_baseline: the union-find oracle over every instance of the batch,
+    whole instances spread over the host's cores; it also checks every label
+    of the last timed step."""
     import torch
     dist = None
     if world > 1:
@@ -524,7 +555,6 @@ def run_batched(args, rank, world, local):
     rp = torch.from_numpy(b.row_ptr).to(dev)
     ci = torch.from_numpy(b.col_idx).to(dev)
     bits = torch.from_numpy(b.open_bits.view(np.int32)).to(dev)
-    abits_d = torch.from_numpy(abits.view(np.int32)).to(dev)
     labels = torch.empty(b.n_total, dtype=torch.int32, device=dev)
     ctx = ccl.ccl_context_create(local)
     stream = torch.cuda.current_stream(dev)
@@ -533,6 +563,9 @@ def run_batched(args, rank, world, local):
         st_t, best_ms = ccl.ccl_autotune_batched(ctx, b.k, b.site_off, b.ent_off, rp, ci, bits, labels, stream)
         ccl.check(st_t, "ccl_autotune_batched")
         tuned = {"best_ms": best_ms}
+    opts = {name: ccl.ccl_get_option(ctx, o) for name, o in (
+        ("pre_analysis", ccl.CCL_OPT_PRE_ANALYSIS), ("link_mode", ccl.CCL_OPT_LINK_MODE),
+        ("refill", ccl.CCL_OPT_REFILL), ("analysis_order", ccl.CCL_OPT_ANALYSIS_ORDER))}
 
     def step():
         st = ccl.ccl_label_batched(ctx, b.k, b.site_off, b.ent_off, rp, ci, bits, labels, stream)
@@ -543,6 +576,10 @@ def run_batched(args, rank, world, local):
         step()
     ccl.check(ccl.ccl_sync(ctx, stream), "warm-up")
     q = int(ccl.ccl_get_stats(ctx).residual_pairs)
+
+    # timed region: per-step CUDA events on the launching stream; the library
+    # records events between its kernels for every timed step (profiling ring)
+    ccl.ccl_set_option(ctx, ccl.CCL_OPT_PROFILE, 1)
     clocks = ClockSampler(local)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -560,20 +597,34 @@ def run_batched(args, rank, world, local):
     clk = clocks.stop()
     ccl.check(ccl.ccl_sync(ctx, stream), "timed steps")
     ms = max_over_ranks(sum(a.elapsed_time(c) for a, c in ev) / args.steps, dist, dev)
+    kern = ccl.ccl_get_step_times(ctx)
+    ccl.ccl_set_option(ctx, ccl.CCL_OPT_PROFILE, 0)
     got = labels.cpu().numpy()
+
+    # graph replay of the same call (the production path), for comparison
+    step()
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(max(1, min(args.steps, 5))):
+        step()
+    g1.record(stream)
+    torch.cuda.synchronize()
+    ms_graph = g0.elapsed_time(g1) / max(1, min(args.steps, 5))
 
     # one instance per call (graphs off: every instance is a new shape)
     one = ccl.ccl_context_create(local)
     ccl.ccl_set_option(one, ccl.CCL_OPT_USE_GRAPHS, 0)
     out1 = torch.empty_like(labels)
-    rp0, ci0, ab0, lab0 = rp.data_ptr(), ci.data_ptr(), abits_d.data_ptr(), out1.data_ptr()
+    rp0, ci0, ab0, lab0 = rp.data_ptr(), ci.data_ptr(), torch.from_numpy(abits.view(np.int32)).to(dev), out1.data_ptr()
+    ab0p = ab0.data_ptr()
     so, eo = b.site_off, b.ent_off
 
     def one_step():
         for k in range(b.k):
             n_k, nnz_k = int(so[k + 1] - so[k]), int(eo[k + 1] - eo[k])
             st = ccl.ccl_label(one, n_k, nnz_k, rp0 + 4 * (int(so[k]) + k), ci0 + 4 * int(eo[k]),
-                               ab0 + 4 * int(word_off[k]), lab0 + 4 * int(so[k]), stream)
+                               ab0p + 4 * int(word_off[k]), lab0 + 4 * int(so[k]), stream)
             if st != ccl.CCL_OK:
                 raise ccl.CclError(st, "ccl_label")
 
@@ -581,6 +632,8 @@ def run_batched(args, rank, world, local):
     ccl.check(ccl.ccl_sync(one, stream), "one-at-a-time warm-up")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = max(1, min(args.steps, 3))
+    if dist:
+        dist.barrier()
     e0.record(stream)
     for _ in range(reps):
         one_step()
@@ -588,47 +641,88 @@ def run_batched(args, rank, world, local):
     torch.cuda.synchronize()
     ms_one = max_over_ranks(e0.elapsed_time(e1) / reps, dist, dev)
     same = bool(torch.equal(out1, labels))
+    del out1, ab0
+    ccl.ccl_context_destroy(one)
 
-    # a seeded sample of instances for the CPU-baseline leg (and its parity check)
-    rng = np.random.default_rng(11 + rank)
-    sample = sorted(rng.choice(b.k, size=min(args.parity_sample, b.k), replace=False).tolist())
-    ok = None
+    # end to end from page-locked host arrays through ccl_label_batched_host;
+    # the device copies of the inputs are dropped first (the context keeps
+    # buffers of its own for the host path)
+    del rp, ci, bits
+    torch.cuda.empty_cache()
+    h_lab = np.empty(b.n_total, np.int32)
+    unpin = _pin([b.row_ptr, b.col_idx, b.open_bits, h_lab])
+    h2d = b.row_ptr.nbytes + b.col_idx.nbytes + b.open_bits.nbytes
+    d2h = h_lab.nbytes
+
+    def e2e_step():
+        st = ccl.ccl_label_batched_host(ctx, b.k, b.site_off, b.ent_off, b.row_ptr, b.col_idx, b.open_bits,
+                                        h_lab, stream)
+        if st != ccl.CCL_OK:
+            raise ccl.CclError(st, "ccl_label_batched_host")
+
+    e2e_step()
+    e_steps = max(1, min(args.steps, 3))
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        e2e_step()
+    e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / e_steps, dist, dev)
+    unpin()
+    e2e_same = bool(np.array_equal(h_lab, got))
+
     if rank == 0:
-        cpu = None
+        peak, peak_src = _peaks()
+        ab = algorithmic_bytes(b.n_total, b.nnz_total, q, "csr", rows=b.n_total + b.k)
+        names = ["init", "analysis_ii", "reduce", "analysis_iv"]
+        dom = max(range(4), key=lambda i: kern[i] if kern[i] > 0.005 else -1)
+        dom_name = names[dom]
+        achieved = ab[dom_name] / (kern[dom] / 1e3) / 1e9
+        traffic, scaled = _ncu_traffic(dom_name, "batched")
+        kernels = {names[i]: ({"ms": kern[i], "alg_bytes": ab[names[i]],
+                               "alg_gbs": ab[names[i]] / (kern[i] / 1e3) / 1e9}
+                              if kern[i] > 0.005 else {"ms": kern[i], "skipped": True})
+                   for i in range(4)}
+        cpu, ok = None, None
         if not args.no_cpu_baseline and world == 1:      # the CPU baseline is an N=1 figure
             import oracle
-            inst = [b.instance(k) for k in sample]      # built before the clock starts
-            t0, done, sites = time.perf_counter(), 0, 0
-            want = {}
-            for k, lat in zip(sample, inst):
-                want[k] = oracle.uf_label(lat)
-                sites += lat.n
-                done += 1
-                if time.perf_counter() - t0 > args.cpu_seconds:
-                    break
-            el = time.perf_counter() - t0
-            for k, lat in zip(sample, inst):           # the rest of the sample, untimed
-                if k not in want:
-                    want[k] = oracle.uf_label(lat)
-            ok = all(np.array_equal(got[int(so[k]):int(so[k + 1])], want[k]) for k in sample)
-            cpu = {"value": sites / el, "unit": "sites/s", "cores": 1, "kind": "oracle",
-                   "sample": f"union-find oracle over {done} instances of the batch ({sites} sites), 1 thread"}
+            t2 = time.perf_counter()
+            want, threads = oracle.uf_label_batched_threads(b)
+            el = time.perf_counter() - t2
+            ok = bool(np.array_equal(got, want))
+            cpu = {"value": b.n_total / el, "unit": "sites/s", "cores": threads, "kind": "oracle",
+                   "sample": f"union-find oracle over all {b.k} instances of the batch ({b.n_total} sites) "
+                             f"in {el:.1f} s, whole instances spread over {threads} threads"}
         line = {
-            "metric": "sites labeled/s (batched)", "value": world * b.n_total / (ms / 1e3), "unit": "sites/s",
+            "metric": METRIC, "value": world * b.n_total / (ms / 1e3), "unit": "sites/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
             "config": {"workload": "batched", "instances": b.k, "n_sites": b.n_total, "nnz": b.nnz_total,
-                       "residual_pairs": q, "generation_s": t_gen, "autotune": tuned,
-                       "l2": "inputs larger than L2 (no flush)"},
-            "one_at_a_time": {"ms_per_step": ms_one, "value": world * b.n_total / (ms_one / 1e3),
-                              "calls_per_step": b.k, "speedup_batched": ms_one / ms,
-                              "labels_identical": same},
-            "path_alg_gbs": algorithmic_bytes(b.n_total, b.nnz_total, q)["path"] / (ms / 1e3) / 1e9,
+                       "desc": "4096 mixed honeycomb / triangle / Cayley-tree instances at p_c +- 0.05, "
+                               "concatenated CSR with int64 offsets",
+                       "residual_pairs": q, "generation_s": t_gen, "options": opts, "autotune": tuned,
+                       "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": f"replicas{world}" if world > 1 else "single"},
+            "one_at_a_time": {"value": world * b.n_total / (ms_one / 1e3), "unit": "sites/s",
+                              "ms_per_step": ms_one, "calls_per_step": b.k, "entry": "ccl_label",
+                              "speedup_batched": ms_one / ms, "labels_identical": same},
+            "edges_per_s": world * (b.nnz_total // 2) / (ms / 1e3),
+            "path_alg_gbs": ab["path"] / (ms / 1e3) / 1e9,
+            "ms_per_step_graph_replay": ms_graph,
+            "kernels": kernels,
+            "roofline": {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "alg_bytes_per_launch": ab[dom_name],
+                         "peak_source": f"{peak_src} hbm_gbs (copy, burst)", "traffic_note": scaled},
             "cpu_baseline": cpu,
-            "gpu_launches": args.steps * 4,
+            "e2e": {"value": world * b.n_total / (e_ms / 1e3), "unit": "sites/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e_ms,
+                    "entry": "ccl_label_batched_host (page-locked host arrays)",
+                    "labels_identical": e2e_same},
+            "gpu_launches": args.steps * (4 if opts["pre_analysis"] else 3),
             "clocks": clk,
-            "parity_sample": {"instances": len(sample), "ok": ok},
+            "parity_all_instances": ok,       # every label of the last timed step vs the oracle
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -804,9 +898,11 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=sorted(CONFIGS) + ["batched", "served"], default="tri4096")
+    ap.add_argument("--config", choices=sorted(CONFIGS) + ["batched", "served"], default="batched")
     ap.add_argument("--instances", type=int, default=4096)
-    ap.add_argument("--parity-sample", type=int, default=48)
+    ap.add_argument("--parity-sample", type=int, default=48, help="served: requests checked per mode")
+    ap.add_argument("--reference-instances", type=int, default=512,
+                    help="reference arm, batched: instances of the mix labelled per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-autotune", action="store_true")

@@ -101,10 +101,16 @@ typedef enum {
                                   residual pairs and loads its next one ahead; 0 a warp hands its
                                   pairs out in order to whichever threads are free (balances
                                   uneven chains) */
-    CCL_OPT_ANALYSIS_ORDER = 7 /* steps (ii)/(iv): 1 (default) each warp walks a contiguous range of
+    CCL_OPT_ANALYSIS_ORDER = 7, /* steps (ii)/(iv): 1 (default) each warp walks a contiguous range of
                                   sites in increasing order (chains meet roots it already stored);
                                   0 the sites are interleaved over the warps (balances inputs
                                   without locality) */
+    CCL_OPT_ITER_CAP = 8       /* 0 (default): the loops of steps (ii)-(iv) stop only at caps
+                                  derived from the input size, which a valid input never reaches.
+                                  v > 0: a chase of step (ii)/(iv) gives up after v iterations and
+                                  a warp of step (iii) abandons its window after v rounds, latching
+                                  CCL_ERR_NONCONVERGED (ccl_sync); the labels are then incomplete.
+                                  For testing the failure path; setting it drops cached graphs. */
 } ccl_option;
 
 CCL_API ccl_status ccl_set_option(ccl_context *ctx, int option, int64_t value);
@@ -202,6 +208,23 @@ CCL_API ccl_status ccl_label_host(ccl_context *ctx, int32_t n_sites, int64_t nnz
                           void *stream);
 
 /*
+ * ccl_label_batched_host -- ccl_label_batched on HOST arrays (the same
+ * layout, offsets and meaning): copies the concatenated inputs to context
+ * buffers, labels, copies the labels back to `labels` (HOST
+ * int32[site_off[K]]) and waits. Synchronous. The bit words go up first, then
+ * the row pointers and columns in four groups of instances of about equal
+ * site counts; step (i) on a group starts as soon as the group has arrived,
+ * while the later groups are still being copied. The context keeps device
+ * buffers of the inputs' size (plus the labels) for later calls. Pinned
+ * host memory gives the full copy bandwidth. Errors: as ccl_label_batched,
+ * plus the device status of ccl_sync.
+ */
+CCL_API ccl_status ccl_label_batched_host(ccl_context *ctx, int32_t n_inst, const int64_t *site_off,
+                                          const int64_t *ent_off, const int32_t *row_ptr,
+                                          const int32_t *col_idx, const uint32_t *open_bits,
+                                          int32_t *labels, void *stream);
+
+/*
  * ccl_label_noalloc -- ccl_label for callers that cannot allocate device
  * memory at run time (the paper has no counterpart; it is a deployment aid).
  * Some programs must not call cudaMalloc once running: a latency-bound loop
@@ -269,6 +292,20 @@ CCL_API ccl_status ccl_validate(ccl_context *ctx, int32_t n_sites, int64_t nnz, 
  */
 CCL_API ccl_status ccl_relabel(ccl_context *ctx, int32_t n, const int32_t *labels, int32_t *seq,
                                int32_t *n_clusters, int32_t *sizes, void *stream);
+
+/*
+ * ccl_largest_cluster -- the largest cluster of finished canonical labels
+ * (the largest-cluster statistic of Section 4's threshold study):
+ * result[0] = its number of sites, result[1] = its label (the smallest label
+ * when several clusters share the largest size); {0, -1} when n = 0.
+ *   labels  DEVICE int32[n], canonical labels (ccl_label output)
+ *   result  DEVICE int32[2], output
+ * Uses 4n + 16 bytes of context scratch (grown with cudaMalloc when needed).
+ * Out-of-range labels are skipped and latched as CCL_ERR_INDEX_OUT_OF_RANGE
+ * (ccl_sync). Asynchronous on `stream`.
+ */
+CCL_API ccl_status ccl_largest_cluster(ccl_context *ctx, int32_t n, const int32_t *labels, int32_t *result,
+                                       void *stream);
 
 /*
  * ccl_spanning -- the spanning test of Section 4: *result = the smallest label

@@ -2,8 +2,8 @@
 
 Plain numpy over labels produced by either side: cluster counts, the
 sequential numbering of clusters with their sizes (the renumbering at the end
-of Section 3) and the spanning test behind the R_span(p) curves (Section 4,
-Figs. 5-6).
+of Section 3), the largest cluster, and the spanning test behind the
+R_span(p) curves (Section 4, Figs. 5-6).
 """
 from __future__ import annotations
 
@@ -20,6 +20,17 @@ def sequential(labels: np.ndarray):
     sizes: np.unique sorts the distinct canonical labels ascending."""
     uniq, inverse, counts = np.unique(labels, return_inverse=True, return_counts=True)
     return inverse.astype(np.int32), counts.astype(np.int32)
+
+
+def largest_cluster(labels: np.ndarray) -> tuple[int, int]:
+    """(size, label) of the largest cluster: the most frequent canonical label,
+    the smallest such label on ties (np.argmax returns the first maximum);
+    (0, -1) for no sites."""
+    if labels.size == 0:
+        return 0, -1
+    counts = np.bincount(labels, minlength=labels.size)
+    lab = int(np.argmax(counts))
+    return int(counts[lab]), lab
 
 
 def spanning_label(labels: np.ndarray, top: np.ndarray, bottom: np.ndarray) -> int:

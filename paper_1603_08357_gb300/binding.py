@@ -37,6 +37,7 @@ CCL_OPT_CTAS_PER_SM = 4
 CCL_OPT_LINK_MODE = 5
 CCL_OPT_REFILL = 6
 CCL_OPT_ANALYSIS_ORDER = 7
+CCL_OPT_ITER_CAP = 8
 
 
 class CclError(RuntimeError):
@@ -92,6 +93,7 @@ def _load() -> ctypes.CDLL:
         "ccl_label": (C, [P, I32, I64, P, P, P, P, P]),
         "ccl_label_batched": (C, [P, I32, P, P, P, P, P, P, P]),
         "ccl_label_host": (C, [P, I32, I64, P, P, P, P, P]),
+        "ccl_label_batched_host": (C, [P, I32, P, P, P, P, P, P, P]),
         "ccl_label_random": (C, [P, I32, I64, P, P, ctypes.c_uint64, ctypes.c_double, P, P]),
         "ccl_label_dense": (C, [P, I32, I32, P, P, P, P]),
         "ccl_label_dense_random": (C, [P, I32, I32, P, ctypes.c_uint64, ctypes.c_double, P, P]),
@@ -99,6 +101,7 @@ def _load() -> ctypes.CDLL:
         "ccl_reserve": (C, [P, I64, I64, I64]),
         "ccl_relabel": (C, [P, I32, P, P, P, P, P]),
         "ccl_spanning": (C, [P, I32, P, P, I32, P, I32, P, P]),
+        "ccl_largest_cluster": (C, [P, I32, P, P, P]),
         "ccl_sync": (C, [P, P, I64]),
         "ccl_validate": (C, [P, I32, I64, P, P, P, P]),
         "ccl_get_stats": (C, [P, ctypes.POINTER(ccl_run_stats)]),
@@ -308,6 +311,20 @@ def ccl_label_host(ctx, n_sites: int, nnz: int, row_ptr, col_idx, open_bits, lab
                                _host_ptr(labels, "labels", np.int32), _stream(stream))
 
 
+def ccl_label_batched_host(ctx, n_inst: int, site_off, ent_off, row_ptr, col_idx, open_bits, labels,
+                           stream=None) -> int:
+    """ccl_label_batched on host arrays; synchronous (see ccl.h)."""
+    so = np.ascontiguousarray(site_off, dtype=np.int64)
+    eo = np.ascontiguousarray(ent_off, dtype=np.int64)
+    if so.size != n_inst + 1 or eo.size != n_inst + 1:
+        return CCL_ERR_INVALID_ARGUMENT
+    return _lib.ccl_label_batched_host(ctx, int(n_inst), so.ctypes.data, eo.ctypes.data,
+                                       _host_ptr(row_ptr, "row_ptr", np.int32),
+                                       _host_ptr(col_idx, "col_idx", np.int32),
+                                       _host_ptr(open_bits, "open_bits", np.uint32),
+                                       _host_ptr(labels, "labels", np.int32), _stream(stream))
+
+
 def ccl_label_noalloc(n_sites: int, nnz: int, row_ptr, col_idx, open_bits, labels, stream=None) -> int:
     """Allocation-free, synchronous single-instance labelling (see ccl.h)."""
     return _lib.ccl_label_noalloc(int(n_sites), int(nnz), _dev_ptr(row_ptr, "row_ptr", _i32()),
@@ -330,6 +347,12 @@ def ccl_spanning(ctx, n: int, labels, top, n_top: int, bottom, n_bottom: int, re
     return _lib.ccl_spanning(ctx, int(n), _dev_ptr(labels, "labels", _i32()), _dev_ptr(top, "top", _i32()),
                              int(n_top), _dev_ptr(bottom, "bottom", _i32()), int(n_bottom),
                              _dev_ptr(result, "result", _i32()), _stream(stream))
+
+
+def ccl_largest_cluster(ctx, n: int, labels, result, stream=None) -> int:
+    """result: DEVICE int32[2] <- (size, label) of the largest cluster."""
+    return _lib.ccl_largest_cluster(ctx, int(n), _dev_ptr(labels, "labels", _i32()),
+                                    _dev_ptr(result, "result", _i32()), _stream(stream))
 
 
 def ccl_sync(ctx, stream=None, timeout_ms: int = -1) -> int:

@@ -87,6 +87,7 @@ struct ccl_context {
     TuneChoice opt;
     int use_graphs = 1;
     int profile = 0;
+    int32_t iter_cap = 0;       // CCL_OPT_ITER_CAP
     std::map<int64_t, TuneChoice> tune_table;
     // graphs
     std::vector<GraphEntry> graphs;
@@ -413,6 +414,31 @@ bool stream_capturing(cudaStream_t s) {
     return cs != cudaStreamCaptureStatusNone;
 }
 
+// Uploads an instance table to ctx->d_insts on stream s through the pinned
+// staging buffer, after the previous upload has left that buffer.
+ccl_status upload_table(ccl_context *ctx, const std::vector<Inst> &table, cudaStream_t s) {
+    const int64_t K = (int64_t)table.size();
+    if (K > ctx->h_insts_cap) {
+        if (ctx->h_insts) { cudaEventSynchronize(ctx->staging_free); cudaFreeHost(ctx->h_insts); }
+        ctx->h_insts = nullptr;
+        ctx->h_insts_cap = 0;
+        CCL_CUDA(cudaMallocHost(&ctx->h_insts, (size_t)K * sizeof(Inst)));
+        ctx->h_insts_cap = K;
+    }
+    if (K > ctx->insts_cap) {
+        if (ctx->d_insts) cudaFree(ctx->d_insts);
+        ctx->d_insts = nullptr;
+        ctx->insts_cap = 0;
+        CCL_CUDA(cudaMalloc(&ctx->d_insts, (size_t)K * sizeof(Inst)));
+        ctx->insts_cap = K;
+    }
+    CCL_CUDA(cudaEventSynchronize(ctx->staging_free));
+    memcpy(ctx->h_insts, table.data(), (size_t)K * sizeof(Inst));
+    CCL_CUDA(cudaMemcpyAsync(ctx->d_insts, ctx->h_insts, (size_t)K * sizeof(Inst), cudaMemcpyHostToDevice, s));
+    CCL_CUDA(cudaEventRecord(ctx->staging_free, s));
+    return CCL_OK;
+}
+
 // Runs P on stream s: through a cached graph when allowed, else directly.
 ccl_status run(ccl_context *ctx, Params P, bool batched, const TuneChoice &tc, cudaStream_t s,
                const std::vector<Inst> *table, uint64_t shape_hash, bool allow_graph = true,
@@ -424,28 +450,8 @@ ccl_status run(ccl_context *ctx, Params P, bool batched, const TuneChoice &tc, c
     const bool capturing = stream_capturing(s);
     if (ctx->profile || !ctx->use_graphs || capturing || !allow_graph) {
         if (batched) {
-            // upload the table through pinned staging; wait until the previous
-            // upload has left the staging buffer before overwriting it
-            const int64_t K = (int64_t)table->size();
-            if (K > ctx->h_insts_cap) {
-                if (ctx->h_insts) { cudaEventSynchronize(ctx->staging_free); cudaFreeHost(ctx->h_insts); }
-                ctx->h_insts = nullptr;
-                ctx->h_insts_cap = 0;
-                CCL_CUDA(cudaMallocHost(&ctx->h_insts, (size_t)K * sizeof(Inst)));
-                ctx->h_insts_cap = K;
-            }
-            if (K > ctx->insts_cap) {
-                if (ctx->d_insts) cudaFree(ctx->d_insts);
-                ctx->d_insts = nullptr;
-                ctx->insts_cap = 0;
-                CCL_CUDA(cudaMalloc(&ctx->d_insts, (size_t)K * sizeof(Inst)));
-                ctx->insts_cap = K;
-            }
-            CCL_CUDA(cudaEventSynchronize(ctx->staging_free));
-            memcpy(ctx->h_insts, table->data(), (size_t)K * sizeof(Inst));
-            CCL_CUDA(cudaMemcpyAsync(ctx->d_insts, ctx->h_insts, (size_t)K * sizeof(Inst),
-                                     cudaMemcpyHostToDevice, s));
-            CCL_CUDA(cudaEventRecord(ctx->staging_free, s));
+            ccl_status st = upload_table(ctx, *table, s);
+            if (st != CCL_OK) return st;
             P.insts = ctx->d_insts;
         }
         if (ctx->profile) {
@@ -522,6 +528,7 @@ Params base_params(ccl_context *ctx, const TuneChoice &tc) {
     P.gen_thr = kNoGen;
     P.err = ctx->d_err;
     P.counters = ctx->d_counters;
+    P.iter_cap = ctx->iter_cap;
     return P;
 }
 
@@ -789,6 +796,14 @@ ccl_status ccl_set_option(ccl_context *ctx, int option, int64_t value) {
         case CCL_OPT_LINK_MODE: ctx->opt.link_mode = value ? 1 : 0; break;
         case CCL_OPT_REFILL: ctx->opt.refill = value ? 1 : 0; break;
         case CCL_OPT_ANALYSIS_ORDER: ctx->opt.ana_seq = value ? 1 : 0; break;
+        case CCL_OPT_ITER_CAP:
+            if (value < 0 || value > INT32_MAX) return CCL_ERR_INVALID_ARGUMENT;
+            ctx->iter_cap = (int32_t)value;
+            {
+                DeviceGuard guard(ctx->device);
+                drop_graphs(ctx);     // captured graphs hold the old cap
+            }
+            return CCL_OK;            // does not touch the tuning table
         default: return CCL_ERR_INVALID_ARGUMENT;
     }
     // explicit options take effect over any tuned entry
@@ -807,6 +822,7 @@ ccl_status ccl_get_option(ccl_context *ctx, int option, int64_t *value) {
         case CCL_OPT_LINK_MODE: *value = ctx->opt.link_mode; break;
         case CCL_OPT_REFILL: *value = ctx->opt.refill; break;
         case CCL_OPT_ANALYSIS_ORDER: *value = ctx->opt.ana_seq; break;
+        case CCL_OPT_ITER_CAP: *value = ctx->iter_cap; break;
         default: return CCL_ERR_INVALID_ARGUMENT;
     }
     return CCL_OK;
@@ -832,17 +848,17 @@ ccl_status ccl_label(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t *ro
 }
 
 namespace {
-// ccl_label_batched with the launch settings given (tc) or looked up (null)
-ccl_status label_batched(ccl_context *ctx, int32_t K, const int64_t *site_off, const int64_t *ent_off,
-                         const int32_t *row_ptr, const int32_t *col_idx, const uint32_t *bits,
-                         int32_t *labels, void *stream, const TuneChoice *force_tc) {
-    if (!ctx || K < 0) return CCL_ERR_INVALID_ARGUMENT;
-    if (K == 0) { ctx->last = ccl_run_stats{}; return CCL_OK; }
-    if (!site_off || !ent_off) return CCL_ERR_INVALID_ARGUMENT;
+// The instance table of a batched call over the concatenated arrays (row_ptr,
+// col_idx, bits, labels; any may be null when the matching total is 0), with
+// the running chunk and tile counts. Checks the offsets.
+ccl_status batch_table(int32_t K, const int64_t *site_off, const int64_t *ent_off, const int32_t *row_ptr,
+                       const int32_t *col_idx, const uint32_t *bits, int32_t *labels, std::vector<Inst> &table,
+                       int64_t &chunks, int64_t &tiles) {
     if (site_off[0] != 0 || ent_off[0] != 0) return CCL_ERR_INVALID_ARGUMENT;
-    std::vector<Inst> table;
+    table.clear();
     table.reserve((size_t)K);
-    int64_t chunks = 0, tiles = 0;
+    chunks = 0;
+    tiles = 0;
     const int64_t rp_len = site_off[K] + K, ci_len = ent_off[K], bits_len = (ent_off[K] + 31) / 32;
     for (int32_t k = 0; k < K; ++k) {
         const int64_t n = site_off[k + 1] - site_off[k];
@@ -867,6 +883,21 @@ ccl_status label_batched(ccl_context *ctx, int32_t K, const int64_t *site_off, c
     const int64_t n_tot = site_off[K], nnz_tot = ent_off[K];
     if (n_tot > 0 && (!row_ptr || !labels)) return CCL_ERR_INVALID_ARGUMENT;
     if (nnz_tot > 0 && (!col_idx || !bits)) return CCL_ERR_INVALID_ARGUMENT;
+    return CCL_OK;
+}
+
+// ccl_label_batched with the launch settings given (tc) or looked up (null)
+ccl_status label_batched(ccl_context *ctx, int32_t K, const int64_t *site_off, const int64_t *ent_off,
+                         const int32_t *row_ptr, const int32_t *col_idx, const uint32_t *bits,
+                         int32_t *labels, void *stream, const TuneChoice *force_tc) {
+    if (!ctx || K < 0) return CCL_ERR_INVALID_ARGUMENT;
+    if (K == 0) { ctx->last = ccl_run_stats{}; return CCL_OK; }
+    if (!site_off || !ent_off) return CCL_ERR_INVALID_ARGUMENT;
+    std::vector<Inst> table;
+    int64_t chunks = 0, tiles = 0;
+    ccl_status st0 = batch_table(K, site_off, ent_off, row_ptr, col_idx, bits, labels, table, chunks, tiles);
+    if (st0 != CCL_OK) return st0;
+    const int64_t n_tot = site_off[K], nnz_tot = ent_off[K];
     ctx->last = ccl_run_stats{};
     ctx->last.n_inst = K;
     ctx->last.n_sites = n_tot;
@@ -1033,6 +1064,28 @@ ccl_status ccl_spanning(ccl_context *ctx, int32_t n, const int32_t *labels, cons
     return CCL_OK;
 }
 
+ccl_status ccl_largest_cluster(ccl_context *ctx, int32_t n, const int32_t *labels, int32_t *result,
+                               void *stream) {
+    if (!ctx || n < 0 || !result) return CCL_ERR_INVALID_ARGUMENT;
+    if (n > 0 && !labels) return CCL_ERR_INVALID_ARGUMENT;
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    // scratch: the 64-bit best key, then one count per site
+    ccl_status st = ensure_aux(ctx, 16 + (int64_t)n * (int64_t)sizeof(int32_t));
+    if (st != CCL_OK) return st;
+    unsigned long long *best = (unsigned long long *)ctx->d_aux;
+    int32_t *cnt = (int32_t *)((char *)ctx->d_aux + 16);
+    CCL_CUDA(cudaMemsetAsync(ctx->d_aux, 0, 16 + (size_t)n * sizeof(int32_t), s));
+    if (n > 0) {
+        const int64_t g = std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * 8, ((int64_t)n + 255) / 256));
+        k_label_counts<<<(unsigned)g, 256, 0, s>>>(n, labels, cnt, ctx->d_err);
+        k_largest<<<(unsigned)g, 256, 0, s>>>(n, cnt, best);
+    }
+    k_largest_finish<<<1, 1, 0, s>>>(best, result);
+    CCL_CUDA(cudaGetLastError());
+    return CCL_OK;
+}
+
 ccl_status ccl_sync(ccl_context *ctx, void *stream, int64_t timeout_ms) {
     if (!ctx) return CCL_ERR_INVALID_ARGUMENT;
     DeviceGuard guard(ctx->device);
@@ -1176,6 +1229,117 @@ ccl_status ccl_label_host(ccl_context *ctx, int32_t n, int64_t nnz, const int32_
         st = label_single(ctx, n, nnz, d_rp, nnz ? d_ci : nullptr, nnz ? d_bits : nullptr, d_lab, s, tc);
     }
     if (st != CCL_OK) return st;
+    CCL_CUDA(cudaMemcpyAsync(labels, d_lab, b_lab, cudaMemcpyDeviceToHost, s));
+    return ccl_sync(ctx, stream, -1);
+}
+
+ccl_status ccl_label_batched_host(ccl_context *ctx, int32_t K, const int64_t *site_off, const int64_t *ent_off,
+                                  const int32_t *row_ptr, const int32_t *col_idx, const uint32_t *bits,
+                                  int32_t *labels, void *stream) {
+    if (!ctx || K < 0) return CCL_ERR_INVALID_ARGUMENT;
+    if (K == 0) { ctx->last = ccl_run_stats{}; return CCL_OK; }
+    if (!site_off || !ent_off) return CCL_ERR_INVALID_ARGUMENT;
+    if (site_off[0] != 0 || ent_off[0] != 0 || site_off[K] < 0 || ent_off[K] < 0) return CCL_ERR_INVALID_ARGUMENT;
+    const int64_t n_tot = site_off[K], nnz_tot = ent_off[K];
+    if (n_tot > 0 && (!row_ptr || !labels)) return CCL_ERR_INVALID_ARGUMENT;
+    if (nnz_tot > 0 && (!col_idx || !bits)) return CCL_ERR_INVALID_ARGUMENT;
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t rp_len = n_tot + K, words = (nnz_tot + 31) / 32;
+    const size_t b_rp = (size_t)rp_len * 4, b_ci = (size_t)nnz_tot * 4, b_bits = (size_t)words * 4,
+                 b_lab = (size_t)n_tot * 4;
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t need = al(b_rp) + al(b_ci) + al(b_bits) + al(b_lab);
+    if ((int64_t)need > ctx->host_in_cap) {
+        CCL_CUDA(cudaStreamSynchronize(s));
+        if (ctx->d_host_in) cudaFree(ctx->d_host_in);
+        ctx->d_host_in = nullptr;
+        ctx->host_in_cap = 0;
+        drop_graphs(ctx);    // graphs may hold pointers into the old buffer
+        CCL_CUDA(cudaMalloc(&ctx->d_host_in, need));
+        ctx->host_in_cap = (int64_t)need;
+    }
+    char *base = (char *)ctx->d_host_in;
+    int32_t *d_rp = (int32_t *)base;
+    int32_t *d_ci = (int32_t *)(base + al(b_rp));
+    uint32_t *d_bits = (uint32_t *)(base + al(b_rp) + al(b_ci));
+    int32_t *d_lab = (int32_t *)(base + al(b_rp) + al(b_ci) + al(b_bits));
+    std::vector<Inst> table;
+    int64_t chunks = 0, tiles = 0;
+    ccl_status st = batch_table(K, site_off, ent_off, d_rp, nnz_tot ? d_ci : nullptr, nnz_tot ? d_bits : nullptr,
+                                d_lab, table, chunks, tiles);
+    if (st != CCL_OK) return st;
+    ctx->last = ccl_run_stats{};
+    ctx->last.n_inst = K;
+    ctx->last.n_sites = n_tot;
+    ctx->last.nnz = nnz_tot;
+    if (chunks == 0) return CCL_OK;
+    const bool batched = K > 1;
+    st = ensure_workspace(ctx, nnz_tot, batched);
+    if (st != CCL_OK) return st;
+    if (!ctx->copy_stream) {
+        CCL_CUDA(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+        for (auto &e : ctx->part_ev) CCL_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    const TuneChoice tc = choice_for_class(ctx, batch_class(n_tot, nnz_tot, K));
+    Params P = base_params(ctx, tc);
+    P.K = K;
+    P.n_chunks = chunks;
+    if (batched) {
+        st = upload_table(ctx, table, s);
+        if (st != CCL_OK) return st;
+        P.insts = ctx->d_insts;
+    } else {
+        P.one = table[0];
+    }
+    CCL_CUDA(cudaMemsetAsync(P.counters, 0, 4 * sizeof(unsigned long long), s));
+    CCL_CUDA(cudaMemsetAsync(P.band, 0, (size_t)kMaxBands * sizeof(BandRec), s));
+    // the uploads may not overwrite the buffers before earlier work on s is done
+    CCL_CUDA(cudaEventRecord(ctx->part_ev[kHostParts], s));
+    CCL_CUDA(cudaStreamWaitEvent(ctx->copy_stream, ctx->part_ev[kHostParts], 0));
+    // all bit words first (nnz/8 bytes), then the rows and columns of the
+    // instances in kHostParts groups of about equal site counts; step (i) on a
+    // group starts when its rows and columns have arrived
+    if (b_bits) CCL_CUDA(cudaMemcpyAsync(d_bits, bits, b_bits, cudaMemcpyHostToDevice, ctx->copy_stream));
+    int32_t band_off = 0;
+    int32_t k0 = 0;
+    for (int part = 0; part < kHostParts; ++part) {
+        int32_t k1 = K;
+        if (part + 1 < kHostParts) {
+            const int64_t target = n_tot * (part + 1) / kHostParts;
+            k1 = (int32_t)(std::upper_bound(site_off, site_off + K + 1, target) - site_off - 1);
+            k1 = std::max(k1, k0);
+        }
+        const int64_t r0 = site_off[k0] + k0, r1 = site_off[k1] + k1;    // row pointers of instances [k0, k1)
+        const int64_t e0 = ent_off[k0], e1 = ent_off[k1];
+        if (r1 > r0)
+            CCL_CUDA(cudaMemcpyAsync(d_rp + r0, row_ptr + r0, (size_t)(r1 - r0) * 4, cudaMemcpyHostToDevice,
+                                     ctx->copy_stream));
+        if (e1 > e0)
+            CCL_CUDA(cudaMemcpyAsync(d_ci + e0, col_idx + e0, (size_t)(e1 - e0) * 4, cudaMemcpyHostToDevice,
+                                     ctx->copy_stream));
+        CCL_CUDA(cudaEventRecord(ctx->part_ev[part], ctx->copy_stream));
+        CCL_CUDA(cudaStreamWaitEvent(s, ctx->part_ev[part], 0));
+        const int64_t t0 = k0 < K ? table[(size_t)k0].tile_begin : tiles;
+        const int64_t t1 = k1 < K ? table[(size_t)k1].tile_begin : tiles;
+        if (t1 > t0) {
+            P.tile_off = t0;
+            P.n_tiles = t1 - t0;
+            P.band_off = band_off;
+            const int64_t g = init_grid(ctx, P, batched, kMaxBands / kHostParts);
+            st = launch_init(P, batched, g, s);
+            if (st != CCL_OK) return st;
+            band_off += (int32_t)g;
+        }
+        k0 = k1;
+    }
+    P.tile_off = 0;
+    P.n_tiles = tiles;
+    P.band_off = 0;
+    P.n_bands = band_off;
+    st = enqueue_tail(ctx, P, batched, tc, s, false);
+    if (st != CCL_OK) return st;
+    CCL_CUDA(cudaEventRecord(ctx->stats_ev, s));
     CCL_CUDA(cudaMemcpyAsync(labels, d_lab, b_lab, cudaMemcpyDeviceToHost, s));
     return ccl_sync(ctx, stream, -1);
 }

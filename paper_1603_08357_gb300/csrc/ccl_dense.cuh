@@ -274,6 +274,7 @@ __device__ __forceinline__ void dense_produce(const Params &P, DenseStage *st, u
                 bulk_g2s(st[s].bw[k], P.one.bits + h.w_lo[k], 4u * (uint32_t)h.w_cnt[k], &full[s]);
         }
     }
+    drain_armed(full, t_local, P.err);
 }
 
 // one lane's site of a staged chunk: slot k's neighbour and its open bit

@@ -123,6 +123,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// Called by the producer lane before it returns: waits (bounded) until the
+// copies of the last kStages tiles it armed (tiles 0 .. n_armed-1 of its
+// band, stage t % kStages) have landed. Copies of earlier tiles have landed
+// already: their stages were released by consumers that waited for them. So
+// the CTA never exits with bulk copies still writing into its shared memory,
+// also when a bounded wait expired and a loop was left early.
+__device__ __forceinline__ void drain_armed(uint64_t *full, int64_t n_armed, unsigned *err) {
+    for (int64_t t = n_armed > kStages ? n_armed - kStages : 0; t < n_armed; ++t)
+        if (!mbar_wait_bounded(&full[t % kStages], (uint32_t)((t / kStages) & 1))) raise_err(err, kErrNonconv);
+}
+
 // 1-D bulk copy global -> shared, completing `bytes` on the mbarrier.
 // dst, src and bytes are multiples of 16.
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
@@ -223,6 +234,7 @@ __device__ __forceinline__ void init_produce(const Params &P, Stage *st, uint64_
         if (b_ci) bulk_g2s(st[s].ci, I.col_idx + h.ci_lo, b_ci, &full[s]);
         if (b_bw) bulk_g2s(st[s].bw, I.bits + h.w_lo, b_bw, &full[s]);
     }
+    drain_armed(full, t_local, P.err);
 }
 
 // General scan of one lane's row (rows longer than kRowRegs, or parts of the
@@ -617,7 +629,7 @@ __global__ void __launch_bounds__(512) k_analysis(Params P) {
                 }
             }
             if (!any) break;
-            if (it > cap) { raise_err(P.err, kErrNonconv); break; }
+            if (it > cap || (P.iter_cap > 0 && it + 1 >= P.iter_cap)) { raise_err(P.err, kErrNonconv); break; }
         }
 #pragma unroll
         for (int u = 0; u < kAnaChunks; ++u)
@@ -697,7 +709,8 @@ __global__ void __launch_bounds__(256) k_reduce(Params P) {
         // A pair needs at most 4n + 8 rounds (its chains and Algorithm 1's loop
         // are bounded by the instance's n <= 32 n_chunks); a lane serves at most
         // wlen pairs. Past this many rounds the window is abandoned with an error.
-        const long long round_cap = (128ll * P.n_chunks + 8) * (long long)wlen;
+        const long long round_cap = P.iter_cap > 0 ? (long long)P.iter_cap
+                                                    : (128ll * P.n_chunks + 8) * (long long)wlen;
         long long rounds = 0;
         // band of the window's first pair (all lanes search; smem broadcast)
         int band = 0;

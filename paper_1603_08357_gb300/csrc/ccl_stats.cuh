@@ -4,7 +4,8 @@
 //    smallest sites (the renumbering the end of Section 3 mentions), plus
 //    the size of every cluster;
 //  * the spanning test of Section 4: the smallest label found both among the
-//    labels of a set of "top" sites and among those of "bottom" sites.
+//    labels of a set of "top" sites and among those of "bottom" sites;
+//  * the largest cluster (its size and label).
 #pragma once
 #include <stdint.h>
 #include <cuda_runtime.h>
@@ -147,6 +148,46 @@ __global__ void k_span_check(int32_t n, const int32_t *__restrict__ lab, const i
 
 __global__ void k_span_finish(int32_t *best) {
     if (*best == INT32_MAX) *best = -1;
+}
+
+// Largest cluster (Section 4's largest-cluster statistic): cnt[l] = sites
+// whose canonical label is l (lanes holding the same label add once), then the
+// largest count over the roots, ties to the smallest label, as one 64-bit key
+// (count << 32) | (0xffffffff - label) under atomicMax.
+__global__ void k_label_counts(int32_t n, const int32_t *__restrict__ lab, int32_t *__restrict__ cnt,
+                               unsigned *err) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
+        const int64_t i = i0 + threadIdx.x;
+        int32_t l = i < n ? __ldg(lab + i) : -1;
+        if (i < n && (uint32_t)l >= (uint32_t)n) { atomicOr(err, kErrIndex); l = -1; }
+        const unsigned peers = __match_any_sync(kFull, l);
+        if (l >= 0 && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicAdd(cnt + l, __popc(peers));
+    }
+}
+
+__global__ void k_largest(int32_t n, const int32_t *__restrict__ cnt, unsigned long long *__restrict__ best) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long key = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int32_t c = __ldg(cnt + i);
+        if (c > 0) {
+            const unsigned long long k = ((unsigned long long)(uint32_t)c << 32) | (0xffffffffu - (uint32_t)i);
+            key = k > key ? k : key;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(kFull, key, o);
+        key = t > key ? t : key;
+    }
+    if ((threadIdx.x & 31) == 0 && key) atomicMax(best, key);
+}
+
+__global__ void k_largest_finish(const unsigned long long *best, int32_t *result) {
+    const unsigned long long k = *best;
+    result[0] = (int32_t)(k >> 32);
+    result[1] = k ? (int32_t)(0xffffffffu - (uint32_t)(k & 0xffffffffu)) : -1;
 }
 
 }  // namespace ccl

@@ -87,7 +87,7 @@ struct Params {
     int64_t nn_width;          // slots per site of the dense list
     int64_t tile_off;          // step (i) on part of the tiles: its first tile ...
     int32_t band_off;          // ... and its first band record
-    int32_t pad2_;
+    int32_t iter_cap;          // > 0: steps (ii)-(iv) give up after this many iterations (test option)
     unsigned *err;
     unsigned long long *counters;   // [0] residual pairs
 };

@@ -1,11 +1,14 @@
 """Section 4 measurements on the GPU: spanning probability R_span(p), its
-crossing point between lattice sizes (the threshold estimate of Figs. 5 and 6)
-and the average time of one realisation at p = 0.5, 1, 1.5 p_c (Fig. 7).
+crossing point between lattice sizes (the threshold estimate of Figs. 5 and 6),
+the largest cluster and the crossing of its finite-size-scaled mean
+S(L, p) L^(-91/48) between sizes (a second threshold estimate), and the
+average time of one realisation at p = 0.5, 1, 1.5 p_c (Fig. 7).
 
 Every realisation runs on the device: ``ccl_label_random`` draws the bonds
 inside step (i) and labels them, ``ccl_spanning`` tests whether one cluster
-touches both the first and the last row of an open-y lattice. Only the 0/1
-spanning flags (one int per realisation) come back to the host.
+touches both the first and the last row of an open-y lattice, and
+``ccl_largest_cluster`` finds the largest cluster. Only three ints per
+realisation come back to the host.
 
 Realisation r at every p uses the same seed (seed0 + r). Since a bond is open
 iff its uniform draw is below p, the realisations are coupled: raising p only
@@ -58,13 +61,33 @@ class Sampler:
         self.stream = stream
         self.dev = dev
 
-    def realise(self, seed: int, p: float, result_addr: int) -> None:
+    def realise(self, seed: int, p: float, result_addr: int, largest_addr: int | None = None) -> None:
         """Labels realisation (seed, p) and writes its spanning label (-1 if
-        none) to the device int at result_addr; asynchronous."""
+        none) to the device int at result_addr and, if largest_addr is given,
+        the size and label of its largest cluster to the two device ints
+        there; asynchronous."""
         B.check(B.ccl_label_random(self.ctx, self.n, self.nnz, self.rp, self.ci, seed, p, self.labels,
                                    self.stream), "ccl_label_random")
         B.check(B.ccl_spanning(self.ctx, self.n, self.labels, self.top, self.top.numel(), self.bot,
                                self.bot.numel(), result_addr, self.stream), "ccl_spanning")
+        if largest_addr is not None:
+            B.check(B.ccl_largest_cluster(self.ctx, self.n, self.labels, largest_addr, self.stream),
+                    "ccl_largest_cluster")
+
+    def sweep(self, ps, n_real: int, seed0: int = 0):
+        """Spanning flags and largest clusters of n_real coupled realisations
+        at each p: returns (span [len(ps), n_real] bool, largest
+        [len(ps), n_real, 2] int32 of (size, label)), one copy back at the end."""
+        import torch
+        res = torch.empty((len(ps), n_real), dtype=torch.int32, device=self.dev)
+        big = torch.empty((len(ps), n_real, 2), dtype=torch.int32, device=self.dev)
+        base, bbase = res.data_ptr(), big.data_ptr()
+        for a, p in enumerate(ps):
+            for r in range(n_real):
+                k = a * n_real + r
+                self.realise(seed0 + r, float(p), base + 4 * k, bbase + 8 * k)
+        B.check(B.ccl_sync(self.ctx, self.stream), "ccl_sync")
+        return (res >= 0).cpu().numpy(), big.cpu().numpy()
 
     def spanning_curve(self, ps, n_real: int, seed0: int = 0) -> np.ndarray:
         """R_span at each p from n_real coupled realisations."""
@@ -104,13 +127,15 @@ class Sampler:
             self.realise(seed, p, addr)
 
 
-def crossing(ps, ra, rb, n_real: int | None = None):
+def crossing(ps, ra, rb, n_real: int | None = None, se=None):
     """p where the curves ra and rb cross: linear interpolation of ra - rb
     between neighbouring grid points where it changes sign, skipping points
     where both curves sit at the same value (0 or 1 far from p_c). Returns
-    (p_x, err) with err the binomial standard error of the two estimates at
-    p_x divided by the difference of the slopes (err is None without
-    n_real), or (None, None) if the curves do not cross."""
+    (p_x, err) with err the standard error of the two estimates at p_x
+    divided by the difference of the slopes -- binomial errors of spanning
+    fractions from n_real realisations, or the given standard errors
+    se = (se_a, se_b) per grid point (err is None with neither) -- or
+    (None, None) if the curves do not cross."""
     ps = np.asarray(ps, np.float64)
     ra, rb = np.asarray(ra, np.float64), np.asarray(rb, np.float64)
     d = ra - rb
@@ -123,14 +148,31 @@ def crossing(ps, ra, rb, n_real: int | None = None):
             else:
                 t = d[a] / (d[a] - d[b])
             x = float(ps[a] + (ps[b] - ps[a]) * t)
-            if n_real is None:
+            if n_real is None and se is None:
                 return x, None
-            r1, r2 = ra[a] + t * (ra[b] - ra[a]), rb[a] + t * (rb[b] - rb[a])
-            var = (r1 * (1 - r1) + r2 * (1 - r2)) / n_real
+            if se is not None:
+                sa, sb = np.asarray(se[0], np.float64), np.asarray(se[1], np.float64)
+                var = (sa[a] + t * (sa[b] - sa[a])) ** 2 + (sb[a] + t * (sb[b] - sb[a])) ** 2
+            else:
+                r1, r2 = ra[a] + t * (ra[b] - ra[a]), rb[a] + t * (rb[b] - rb[a])
+                var = (r1 * (1 - r1) + r2 * (1 - r2)) / n_real
             lo, hi = max(a - 1, 0), min(b + 1, len(ps) - 1)
             dslope = abs((d[hi] - d[lo]) / (ps[hi] - ps[lo]))
             return x, float(np.sqrt(var) / dslope)
     return None, None
+
+
+D_FRACTAL = 91 / 48      # exact fractal dimension of 2-D percolation clusters
+
+
+def scaled_largest(largest_sizes: np.ndarray, L: int):
+    """Mean largest-cluster size over realisations (last axis) scaled by
+    L^-D, with its standard error: at p_c it tends to a constant, so the
+    scaled curves of different L cross there (finite-size scaling)."""
+    v = largest_sizes.astype(np.float64)
+    m = v.mean(axis=-1) / L ** D_FRACTAL
+    e = v.std(axis=-1, ddof=1) / np.sqrt(v.shape[-1]) / L ** D_FRACTAL
+    return m, e
 
 
 def main(argv=None):
@@ -157,19 +199,25 @@ def main(argv=None):
         top, bot = boundary_rows(kind, L)
         smp = Sampler(ctx, lat, top, bot)
         t0 = time.perf_counter()
-        R = smp.spanning_curve(ps, a.realisations, a.seed * 1_000_003 + L)
+        span, big = smp.sweep(ps, a.realisations, a.seed * 1_000_003 + L)
         wall = time.perf_counter() - t0
+        R = span.mean(axis=1)
+        S, S_err = scaled_largest(big[..., 0], L)
         times = {f"{m}pc": smp.time_per_realisation(m * pc, a.timing_reps) for m in (0.5, 1.0, 1.5)}
-        curves[L] = R
+        curves[L] = (R, S, S_err)
         print(json.dumps({"lattice": kind, "L": L, "N": lat.n, "realisations": a.realisations,
                           "p": [round(float(p), 6) for p in ps], "R_span": [round(float(r), 5) for r in R],
+                          "largest_scaled": [round(float(x), 6) for x in S],
                           "ms_per_realisation": {k: round(v, 4) for k, v in times.items()},
                           "sweep_wall_s": round(wall, 2)}), flush=True)
         del smp
         torch.cuda.empty_cache()
-    xs = {f"{sizes[i]}x{sizes[i + 1]}": crossing(ps, curves[sizes[i]], curves[sizes[i + 1]], a.realisations)
-          for i in range(len(sizes) - 1)}
-    print(json.dumps({"lattice": kind, "p_c_exact": round(pc, 6), "crossings": xs}), flush=True)
+    pairs = [(sizes[i], sizes[i + 1]) for i in range(len(sizes) - 1)]
+    xs = {f"{u}x{v}": crossing(ps, curves[u][0], curves[v][0], a.realisations) for u, v in pairs}
+    xl = {f"{u}x{v}": crossing(ps, curves[u][1], curves[v][1], se=(curves[u][2], curves[v][2]))
+          for u, v in pairs}
+    print(json.dumps({"lattice": kind, "p_c_exact": round(pc, 6), "crossings": xs,
+                      "largest_cluster_crossings": xl}), flush=True)
     B.ccl_context_destroy(ctx)
 
 

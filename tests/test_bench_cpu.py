@@ -73,3 +73,32 @@ def test_committed_traffic_is_plausible():
         held = 4 * (n + 1) + 4 * nnz + nnz // 8 + 4 * n + 8 * nnz    # inputs, labels, a full queue
         b = ent["dram_bytes_per_launch"]
         assert 0.05 * 8 * n <= b <= 4 * held, (key, b)
+
+
+def test_batched_row_pointer_bytes():
+    n, nnz, q, K = 1000, 6000, 300, 7
+    one = bench.algorithmic_bytes(n, nnz, q)
+    many = bench.algorithmic_bytes(n, nnz, q, rows=n + K)
+    assert many["init"] - one["init"] == 4 * (K - 1)
+
+
+def test_reference_arm_line_batched():
+    """The reference arm on the default (batched) workload: the oracle over the
+    first instances of the mix, whole instances spread over the host's cores."""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--instances", "64", "--reference-instances", "6", "--steps", "2", "--warmup", "1"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["config"]["workload"] == "batched" and line["cpu_baseline"]["cores"] >= 1
+    sb = L.make_batch(L.batched_mix_specs(64, seed=4)[:6])
+    assert line["config"]["n_sites"] == sb.n_total
+    assert line["value"] > 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_threaded_batched_oracle_equals_serial():
+    import oracle
+    b = L.make_batch(L.batched_mix_specs(40, seed=9))
+    got, threads = oracle.uf_label_batched_threads(b, 3)
+    assert threads == 3 and np.array_equal(got, oracle.uf_label_batched(b))

@@ -65,3 +65,36 @@ def test_maximum_csr_size(ctx):
     torch.cuda.empty_cache()
     want = oracle.uf_label(lat)
     assert np.array_equal(got, want), int(np.count_nonzero(got != want))
+
+
+def test_batched_mix_full_size_matches_oracle():
+    """The whole batched workload: 4096 mixed honeycomb / triangle / Cayley
+    instances (about 2.1e9 sites, 7.3e9 CSR entries) in one ccl_label_batched
+    call with the autotuned settings (graph replay on the second call), every
+    label against the union-find oracle run over all host cores; then the
+    same batch through ccl_label_batched_host."""
+    b = L.make_batch(L.batched_mix_specs(4096, seed=4))
+    want, _ = oracle.uf_label_batched_threads(b)
+    c = ccl.ccl_context_create(0)
+    try:
+        rp = torch.from_numpy(b.row_ptr).to(DEV)
+        ci = torch.from_numpy(b.col_idx).to(DEV)
+        bits = torch.from_numpy(b.open_bits.view(np.int32)).to(DEV)
+        out = torch.empty(b.n_total, dtype=torch.int32, device=DEV)
+        st, _ = ccl.ccl_autotune_batched(c, b.k, b.site_off, b.ent_off, rp, ci, bits, out)
+        assert st == ccl.CCL_OK, ccl.ccl_status_string(st)
+        for _ in range(2):
+            out.fill_(-1)
+            assert ccl.ccl_label_batched(c, b.k, b.site_off, b.ent_off, rp, ci, bits, out) == ccl.CCL_OK
+            assert ccl.ccl_sync(c) == ccl.CCL_OK
+            got = out.cpu().numpy()
+            bad = np.flatnonzero(got != want)
+            assert bad.size == 0, f"{bad.size} labels differ, first at site {bad[0]}"
+        del rp, ci, bits, out
+        torch.cuda.empty_cache()
+        h = np.full(b.n_total, -1, np.int32)
+        st = ccl.ccl_label_batched_host(c, b.k, b.site_off, b.ent_off, b.row_ptr, b.col_idx, b.open_bits, h)
+        assert st == ccl.CCL_OK, ccl.ccl_status_string(st)
+        assert np.array_equal(h, want)
+    finally:
+        ccl.ccl_context_destroy(c)

@@ -207,3 +207,70 @@ def test_stats_after_host_path_grows(ctx):
     assert ccl.ccl_relabel(ctx, small.n, d_lab, seq, nc) == ccl.CCL_OK
     assert ccl.ccl_sync(ctx) == ccl.CCL_OK
     assert np.array_equal(seq.cpu().numpy(), stats.sequential(lab)[0])
+
+
+def _largest(ctx, lab):
+    res = torch.full((2,), -9, dtype=torch.int32, device=DEV)
+    d = torch.from_numpy(np.ascontiguousarray(lab, np.int32)).to(DEV) if lab.size else \
+        torch.zeros(1, dtype=torch.int32, device=DEV)
+    assert ccl.ccl_largest_cluster(ctx, lab.size, d, res) == ccl.CCL_OK
+    return tuple(int(v) for v in res.cpu().numpy())
+
+
+def test_largest_cluster_matches_oracle(ctx):
+    """ccl_largest_cluster against the oracle's statistic: ties go to the
+    smaller label (the worked example's two 5-site clusters), lattices from
+    p = 0 (all singletons) to p = 1, a randomly numbered tree, sizes across
+    warp and grid edges, and no sites."""
+    from conftest import load_golden
+    g = load_golden("worked_example.txt")
+    assert _largest(ctx, np.array(g["label"], np.int32)) == tuple(g["largest"])
+    assert _largest(ctx, np.zeros(0, np.int32)) == (0, -1)
+    assert _largest(ctx, np.zeros(1, np.int32)) == (1, 0)
+    for lat in (L.triangle(300, 0.0, 1), L.triangle(300, 1.0, 1), L.triangle(257, L.PC_TRIANGLE, 2),
+                L.honeycomb(129, L.PC_HONEYCOMB, 3), L.cayley(3, 14, 0.5, 4, perm_seed=4),
+                L.random_graph(33, 40, 5)):
+        lab = gpu_label(ctx, lat)
+        assert _largest(ctx, lab) == stats.largest_cluster(oracle.uf_label(lat))
+    assert ccl.ccl_sync(ctx) == ccl.CCL_OK
+
+
+def test_largest_cluster_bad_label_is_reported(ctx):
+    lab = np.array([0, 0, 7, 1], np.int32)             # 7 is out of range for n = 4
+    assert _largest(ctx, lab) == (2, 0)
+    assert ccl.ccl_sync(ctx) == ccl.CCL_ERR_INDEX_OUT_OF_RANGE
+
+
+def test_sweep_largest_matches_oracle(ctx):
+    """The device sweep (device-drawn bonds, spanning and largest cluster per
+    realisation) equals, realisation by realisation, the oracle's statistics
+    of the same keyed bonds."""
+    from paper_1603_08357_gb300 import percolation as P
+    for kind, Ls in (("triangle", 40), ("honeycomb", 23)):
+        lat = L.make_instance(dict(kind=kind, L=Ls, p=0.0, seed=0, periodic_y=False))
+        top, bot = P.boundary_rows(kind, Ls)
+        ps = [P.PC_EXACT[kind] - 0.05, P.PC_EXACT[kind], P.PC_EXACT[kind] + 0.05]
+        span, big = P.Sampler(ctx, lat, top, bot).sweep(ps, 60, seed0=900)
+        for a, p in enumerate(ps):
+            for r in range(60):
+                lab = oracle.uf_label(dataclasses.replace(lat, open_bits=oracle.keyed_bits(lat, 900 + r, p)))
+                assert tuple(big[a, r]) == stats.largest_cluster(lab), (kind, p, r)
+                assert bool(span[a, r]) == (stats.spanning_label(lab, top, bot) >= 0)
+
+
+def test_largest_cluster_crossing_near_exact_threshold(ctx):
+    """The finite-size-scaled mean largest cluster S(L, p) L^(-91/48) of two
+    sizes crosses near 2 sin(pi/18) (triangle)."""
+    from paper_1603_08357_gb300 import percolation as P
+    pc = P.PC_EXACT["triangle"]
+    ps = np.linspace(pc - 0.03, pc + 0.03, 7)
+    curves = []
+    for Ls in (64, 128):
+        lat = L.make_instance(dict(kind="triangle", L=Ls, p=0.0, seed=0, periodic_y=False))
+        _, big = P.Sampler(ctx, lat, *P.boundary_rows("triangle", Ls)).sweep(ps, 1500, 31)
+        curves.append(P.scaled_largest(big[..., 0], Ls))
+    for m, _ in curves:
+        assert np.all(np.diff(m) > 0)
+    x, err = P.crossing(ps, curves[0][0], curves[1][0], se=(curves[0][1], curves[1][1]))
+    assert x is not None and err is not None and err < 0.01
+    assert abs(x - pc) < 0.012, (x, err)

@@ -287,6 +287,68 @@ def test_batched_matches_oracle_and_single(ctx, graphs):
     assert pairs == tot
 
 
+@pytest.mark.parametrize("K", [1, 3, 150])
+def test_batched_host_path(ctx, K):
+    """ccl_label_batched_host: host arrays in, labels out, the instances
+    uploaded in four groups with step (i) started per group; equal to the
+    oracle and to the device-array call, twice in a row (buffers reused)."""
+    specs = _mixed_specs(K, 40 + K)
+    if K == 3:
+        specs[1] = dict(kind="triangle", L=0, p=0.5, seed=1)     # an empty instance in the middle
+    b = L.make_batch(specs)
+    want = oracle.uf_label_batched(b)
+    for _ in range(2):
+        out = np.full(b.n_total, -3, np.int32)
+        st = ccl.ccl_label_batched_host(ctx, b.k, b.site_off, b.ent_off, b.row_ptr, b.col_idx,
+                                        b.open_bits, out)
+        assert st == ccl.CCL_OK, ccl.ccl_status_string(st)
+        assert np.array_equal(out, want)
+    assert np.array_equal(gpu_label_batched(ctx, b), want)
+    assert ccl.ccl_get_stats(ctx).n_inst == b.k
+
+
+def test_batched_host_path_large_groups(ctx):
+    """Instances big enough that every upload group holds several step-(i)
+    bands, in a batch whose bits start mid-word for most instances."""
+    specs = [dict(kind="triangle", L=700, p=L.PC_TRIANGLE, seed=1), dict(kind="honeycomb", L=33, p=0.6, seed=2),
+             dict(kind="cayley", z=3, shells=14, p=0.5, seed=3, perm_seed=3),
+             dict(kind="triangle", L=513, p=0.36, seed=4), dict(kind="honeycomb", L=600, p=0.65, seed=5)]
+    b = L.make_batch(specs)
+    out = np.full(b.n_total, -3, np.int32)
+    st = ccl.ccl_label_batched_host(ctx, b.k, b.site_off, b.ent_off, b.row_ptr, b.col_idx, b.open_bits, out)
+    assert st == ccl.CCL_OK, ccl.ccl_status_string(st)
+    assert np.array_equal(out, oracle.uf_label_batched(b))
+
+
+@pytest.mark.parametrize("pre", [0, 1])
+def test_iteration_cap_reports_nonconvergence(pre):
+    """The failure path of the iteration caps (Algorithm 1's merge loop and
+    the root chases of steps (ii)/(iv)): with CCL_OPT_ITER_CAP = 1 a triangle
+    lattice at p_c (long label chains) cannot finish, ccl_sync returns
+    CCL_ERR_NONCONVERGED, single and batched; with the cap cleared the same
+    context labels correctly again."""
+    lat = L.triangle(512, L.PC_TRIANGLE, 3)
+    b = L.make_batch(_mixed_specs(20, 5) + [dict(kind="triangle", L=300, p=L.PC_TRIANGLE, seed=9)])
+    c = ccl.ccl_context_create(0)
+    try:
+        ccl.ccl_set_option(c, ccl.CCL_OPT_PRE_ANALYSIS, pre)
+        assert ccl.ccl_set_option(c, ccl.CCL_OPT_ITER_CAP, 1) == ccl.CCL_OK
+        assert ccl.ccl_get_option(c, ccl.CCL_OPT_ITER_CAP) == 1
+        for _ in range(2):
+            gpu_label(c, lat, expect_status=ccl.CCL_ERR_NONCONVERGED)
+        out = torch.empty(b.n_total, dtype=torch.int32, device=DEV)
+        from ccl_testutil import batch_to_dev
+        brp, bci, bbits = batch_to_dev(b)
+        assert ccl.ccl_label_batched(c, b.k, b.site_off, b.ent_off, brp, bci, bbits, out) == ccl.CCL_OK
+        assert ccl.ccl_sync(c) == ccl.CCL_ERR_NONCONVERGED
+        assert ccl.ccl_set_option(c, ccl.CCL_OPT_ITER_CAP, 0) == ccl.CCL_OK
+        assert np.array_equal(gpu_label(c, lat), oracle.uf_label(lat))
+        assert np.array_equal(gpu_label_batched(c, b), oracle.uf_label_batched(b))
+        assert ccl.ccl_set_option(c, ccl.CCL_OPT_ITER_CAP, -1) == ccl.CCL_ERR_INVALID_ARGUMENT
+    finally:
+        ccl.ccl_context_destroy(c)
+
+
 def test_two_streams_two_contexts():
     c1, c2 = ccl.ccl_context_create(0), ccl.ccl_context_create(0)
     s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()

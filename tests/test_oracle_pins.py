@@ -102,6 +102,8 @@ def test_golden_steps(name):
     assert st["n_residual"] == sum(len(v) for v in res.values())
     assert oracle.uf_label(lat).tolist() == g["label"]
     assert oracle.bfs_label(lat).tolist() == g["label"]
+    if "largest" in g:
+        assert list(stats.largest_cluster(st["label"])) == g["largest"]
 
 
 @pytest.mark.parametrize("seed", range(6))
@@ -213,6 +215,50 @@ def test_spanning_crossing_brackets_pc(kind):
         return 4 * math.sqrt((a * (1 - a) + b * (1 - b)) / n + 1.0 / n ** 2)
     assert lo_s - lo_b > tol(lo_s, lo_b), (lo_s, lo_b)
     assert hi_b - hi_s > tol(hi_s, hi_b), (hi_s, hi_b)
+
+
+def _mean_largest(kind, Ls, p, reps, seed0):
+    """Mean size of the largest cluster over `reps` periodic realisations, and
+    its standard error."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(r):
+        lat = L.make_instance(dict(kind=kind, L=Ls, p=p, seed=seed0 + r), nthreads=1)
+        return stats.largest_cluster(oracle.uf_label(lat))[0]
+    with ThreadPoolExecutor(8) as ex:
+        v = np.array(list(ex.map(one, range(reps))), float)
+    return v.mean(), v.std(ddof=1) / math.sqrt(reps)
+
+
+@pytest.mark.parametrize("kind", ["triangle", "honeycomb"])
+def test_largest_cluster_scales_with_the_fractal_dimension(kind):
+    """At p_c the largest cluster of an L x L system grows as L^D with the
+    exact two-dimensional percolation fractal dimension D = 91/48, so the mean
+    largest cluster at 2L over that at L is 2^(91/48) = 3.7214 up to
+    corrections that are small at L = 64..128 and within CLT error; slightly
+    off p_c the ratio moves far from it (towards 1 below, 4 above). This pins
+    the largest-cluster statistic and, through it, the thresholds
+    1 - 2 sin(pi/18) and 2 sin(pi/18) (Section 4)."""
+    pc = L.PC_TRIANGLE if kind == "triangle" else L.PC_HONEYCOMB
+    target = 2 ** (91 / 48)
+    a, ea = _mean_largest(kind, 64, pc, 2000, 10_000)
+    b, eb = _mean_largest(kind, 128, pc, 2000, 20_000)
+    ratio = b / a
+    err = ratio * math.hypot(ea / a, eb / b)
+    assert abs(ratio - target) < 4 * err + 0.01, (ratio, err)
+    lo = _mean_largest(kind, 128, pc - 0.03, 300, 30_000)[0] / _mean_largest(kind, 64, pc - 0.03, 300, 40_000)[0]
+    hi = _mean_largest(kind, 128, pc + 0.03, 300, 50_000)[0] / _mean_largest(kind, 64, pc + 0.03, 300, 60_000)[0]
+    assert lo < target - 0.8 and hi > target + 0.15, (lo, hi)
+
+
+def test_largest_cluster_extremes():
+    tri = L.triangle(16, 0.0, 1)
+    assert stats.largest_cluster(oracle.uf_label(tri)) == (1, 0)      # singletons: the tie goes to site 0
+    tri = L.triangle(16, 1.0, 1)
+    assert stats.largest_cluster(oracle.uf_label(tri)) == (256, 0)
+    assert stats.largest_cluster(np.zeros(0, np.int32)) == (0, -1)
+    # two clusters {0, 2} and {1, 3, 4}: the larger wins although its label is larger
+    assert stats.largest_cluster(np.array([0, 1, 0, 1, 1], np.int32)) == (3, 1)
 
 
 def test_extremes():

@@ -44,7 +44,7 @@ def test_noalloc_allocates_nothing_after_the_first_call():
     """After the first call on the device (which loads the library's device
     code and with it the fixed array), further calls leave the device's free
     memory unchanged: every buffer here exists before the calls."""
-    lat = L.triangle(700, L.PC_TRIANGLE, 8)
+    lat = L.triangle(560, L.PC_TRIANGLE, 8)     # 1,881,600 entries, within the limit
     rp, ci, bits = to_dev(lat)
     out = torch.full((lat.n,), -5, dtype=torch.int32, device=DEV)
     assert ccl.ccl_label_noalloc(lat.n, lat.nnz, rp, ci, bits, out) == ccl.CCL_OK
