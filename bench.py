@@ -731,13 +731,16 @@ def run_batched(args, rank, world, local):
 
 
 def run_served(args, rank, world, local):
-    """The served workload: requests of log-uniform size (1e3..1e7 sites, the
-    three lattice types at p_c) through the request loop (ccl_server_*),
-    host arrays in, labels back on the host. First the capacity with a
-    bounded number of requests in flight (closed loop), then Poisson arrivals
-    at a fraction of that capacity (open loop) for the latency percentiles.
-    Requests repeat a pool of distinct pre-generated instances (the whole
-    stream would not fit in host memory)."""
+    """The served workload: a stream of requests (log-uniform 1e3..1e7 sites,
+    the three lattice types at p_c) through the request loop (ccl_server_*),
+    host arrays in, labels back in host memory, against the same stream
+    labelled one ccl_label_host call at a time from the same host memory.
+    First the capacity with a bounded number of requests in flight (closed
+    loop, both submission modes), then Poisson arrivals at fractions of that
+    capacity (open loop) for the latency percentiles. The stream repeats a
+    pool of distinct pre-generated requests (the whole stream would not fit in
+    host memory); the pool's arrays are page-locked once, as a serving
+    process keeps its request buffers."""
     import torch
     torch.cuda.set_device(local)
     import paper_1603_08357_gb300 as ccl
@@ -746,42 +749,33 @@ def run_served(args, rank, world, local):
     pool = [L.make_instance(sp) for sp in specs[:args.pool]]
     t_gen = time.perf_counter() - t_gen
     req = [pool[r % len(pool)] for r in range(args.requests)]
-    mean_sites = float(np.mean([lat.n for lat in req]))
+    total_sites = sum(lat.n for lat in req)
+    mean_sites = total_sites / len(req)
     out_bufs = {id(lat): np.empty(lat.n, np.int32) for lat in pool}
+    unpin = _pin([a for lat in pool for a in (lat.row_ptr, lat.col_idx, lat.open_bits)] + list(out_bufs.values()))
+    keep_idx = set(range(0, len(req), max(1, len(req) // args.parity_sample)))
 
-    def submit_nocopy(srv, lat):
-        # the pool's arrays stay alive and unchanged for the whole run
-        while True:
-            st, t = ccl.ccl_server_submit_nocopy(srv, lat.n, lat.nnz, lat.row_ptr, lat.col_idx, lat.open_bits)
-            if st == ccl.CCL_OK:
-                return t
-            if st != ccl.CCL_ERR_REJECTED:
-                raise ccl.CclError(st, "ccl_server_submit_nocopy")
-            time.sleep(0.0005)
+    def submit_with(fn, name):
+        def sub(srv, lat):
+            while True:
+                st, t = fn(srv, lat.n, lat.nnz, lat.row_ptr, lat.col_idx, lat.open_bits)
+                if st == ccl.CCL_OK:
+                    return t
+                if st != ccl.CCL_ERR_REJECTED:
+                    raise ccl.CclError(st, name)
+                time.sleep(0.0005)
+        return sub
+    submit_nocopy = submit_with(ccl.ccl_server_submit_nocopy, "ccl_server_submit_nocopy")
+    submit = submit_with(ccl.ccl_server_submit, "ccl_server_submit")
 
-    def submit(srv, lat):
-        while True:
-            st, t = ccl.ccl_server_submit(srv, lat.n, lat.nnz, lat.row_ptr, lat.col_idx, lat.open_bits)
-            if st == ccl.CCL_OK:
-                return t
-            if st != ccl.CCL_ERR_REJECTED:
-                raise ccl.CclError(st, "ccl_server_submit")
-            time.sleep(0.0005)
-
-    def drain(srv, tickets, lats, keep=None):
-        for k, (t, lat) in enumerate(zip(tickets, lats)):
-            buf = out_bufs[id(lat)] if keep is None or k not in keep else np.empty(lat.n, np.int32)
-            ccl.check(ccl.ccl_server_wait(srv, t, buf, 600_000), "ccl_server_wait")
-            if keep is not None and k in keep:
-                keep[k] = buf
-
-    # closed loop: at most `window` requests in flight
-    clocks = ClockSampler(local)
-
-    def closed_loop(nocopy: bool):
+    def new_server():
         srv = ccl.ccl_server_create(local, n_streams=args.streams, max_batch=1024, host_staging_bytes=4 << 30)
-        sub = submit_nocopy if nocopy else submit
-        drain(srv, [sub(srv, lat) for lat in pool[:16]], pool[:16])
+        for lat in pool[:16]:                                   # warm-up
+            ccl.check(ccl.ccl_server_wait(srv, submit_nocopy(srv, lat), out_bufs[id(lat)], 600_000), "warm-up")
+        return srv
+
+    def closed_loop(sub):
+        srv = new_server()
         tickets = [None] * len(req)
         sem = threading.Semaphore(args.window)
 
@@ -790,16 +784,16 @@ def run_served(args, rank, world, local):
                 sem.acquire()
                 tickets[k] = sub(srv, lat)
 
-        keep = {k: None for k in range(0, len(req), max(1, len(req) // args.parity_sample))}
+        keep = {}
         t0 = time.perf_counter()
         th = threading.Thread(target=feeder)
         th.start()
         for k, lat in enumerate(req):
             while tickets[k] is None:
                 time.sleep(0.00005)
-            buf = np.empty(lat.n, np.int32) if k in keep else out_bufs[id(lat)]
+            buf = np.empty(lat.n, np.int32) if k in keep_idx else out_bufs[id(lat)]
             ccl.check(ccl.ccl_server_wait(srv, tickets[k], buf, 600_000), "ccl_server_wait")
-            if k in keep:
+            if k in keep_idx:
                 keep[k] = buf
             sem.release()
         th.join()
@@ -808,12 +802,32 @@ def run_served(args, rank, world, local):
         ccl.ccl_server_destroy(srv)
         return wall, st, keep
 
+    clocks = ClockSampler(local)
     clocks.start()
-    wall_copy, st_copy, keep_copy = closed_loop(False)
-    wall, st_closed, keep = closed_loop(True)
+    wall, st_closed, keep = closed_loop(submit_nocopy)
+    wall_copy, st_copy, keep_copy = closed_loop(submit)
     clk = clocks.stop()
-    total_sites = sum(lat.n for lat in req)
     capacity = total_sites / wall
+
+    # one request at a time through the host-buffer entry point, same stream
+    one = ccl.ccl_context_create(local)
+    stream = torch.cuda.current_stream()
+    for lat in pool[:16]:
+        ccl.check(ccl.ccl_label_host(one, lat.n, lat.nnz, lat.row_ptr, lat.col_idx, lat.open_bits,
+                                     out_bufs[id(lat)], stream), "ccl_label_host")
+    lat_one, keep_one = [], {}
+    t0 = time.perf_counter()
+    for k, lat in enumerate(req):
+        buf = np.empty(lat.n, np.int32) if k in keep_idx else out_bufs[id(lat)]
+        t1 = time.perf_counter()
+        ccl.check(ccl.ccl_label_host(one, lat.n, lat.nnz, lat.row_ptr, lat.col_idx, lat.open_bits, buf, stream),
+                  "ccl_label_host")
+        lat_one.append(time.perf_counter() - t1)
+        if k in keep_idx:
+            keep_one[k] = buf
+    wall_one = time.perf_counter() - t0
+    ccl.ccl_context_destroy(one)
+    lat_one = np.array(lat_one) * 1e3
 
     # open loop: Poisson arrivals at load x capacity
     loads = {}
@@ -821,8 +835,7 @@ def run_served(args, rank, world, local):
         rate = load * capacity / mean_sites            # requests per second
         rng = np.random.default_rng(55 + rank)
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(req)))
-        srv = ccl.ccl_server_create(local, n_streams=args.streams, max_batch=1024, host_staging_bytes=4 << 30)
-        drain(srv, [submit_nocopy(srv, lat) for lat in pool[:16]], pool[:16])
+        srv = new_server()
         tk = [None] * len(req)
 
         def open_feeder():
@@ -848,6 +861,7 @@ def run_served(args, rank, world, local):
         loads[str(load)] = {"offered_req_per_s": rate, "achieved_sites_per_s": total_sites / el,
                             "p50_ms": so.p50_ms, "p99_ms": so.p99_ms, "max_ms": so.max_ms,
                             "batches": int(so.batches)}
+    unpin()
 
     ok = None
     if rank == 0:
@@ -863,23 +877,30 @@ def run_served(args, rank, world, local):
                     break
             cpu = {"value": sites / (time.perf_counter() - t2), "unit": "sites/s", "cores": 1,
                    "kind": "oracle", "sample": f"union-find oracle over {done} pool requests ({sites} sites), 1 thread"}
-            # the leg's oracle also checks the kept labels of both submission modes
-            ok = all(np.array_equal(buf, oracle.uf_label(req[k])) for kp in (keep, keep_copy) for k, buf in kp.items())
+            # the leg's oracle also checks the kept labels of all three arms
+            ok = all(np.array_equal(kp[k], oracle.uf_label(req[k]))
+                     for kp in (keep, keep_copy, keep_one) for k in keep_idx)
         h2d = sum(4 * (lat.n + 1) + 4 * lat.nnz + 4 * lat.open_bits.size for lat in req) / len(req)
         line = {
-            "metric": "sites labeled/s (served)", "value": world * capacity, "unit": "sites/s",
+            "metric": "sites labeled/s (served vs one-at-a-time)", "value": world * capacity, "unit": "sites/s",
             "n_gpus": world, "steps": len(req), "warmup": 16, "ms_per_step": 1e3 * wall / len(req),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
             "config": {"workload": "served", "requests": len(req), "pool": len(pool),
                        "mean_sites": mean_sites, "window": args.window, "streams": args.streams,
-                       "generation_s": t_gen, "l2": "inputs larger than L2 in aggregate (no flush)"},
+                       "generation_s": t_gen, "host_arrays": "page-locked",
+                       "l2": "inputs larger than L2 in aggregate (no flush)"},
             "closed_loop": {"submit": "ccl_server_submit_nocopy", "wall_s": wall,
                             "requests_per_s": len(req) / wall, "batches": int(st_closed.batches),
                             "p50_ms": st_closed.p50_ms, "p99_ms": st_closed.p99_ms},
             "closed_loop_copying": {"submit": "ccl_server_submit", "sites_per_s": total_sites / wall_copy,
                                     "requests_per_s": len(req) / wall_copy, "batches": int(st_copy.batches),
                                     "p50_ms": st_copy.p50_ms, "p99_ms": st_copy.p99_ms},
+            "one_at_a_time": {"entry": "ccl_label_host, one call per request, same host arrays",
+                              "value": world * total_sites / wall_one, "unit": "sites/s", "wall_s": wall_one,
+                              "requests_per_s": len(req) / wall_one,
+                              "p50_ms": float(np.percentile(lat_one, 50)), "p99_ms": float(np.percentile(lat_one, 99)),
+                              "speedup_served": wall_one / wall},
             "open_loop": loads,
             "e2e": {"value": world * capacity, "unit": "sites/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": 4 * mean_sites,
@@ -887,7 +908,7 @@ def run_served(args, rank, world, local):
             "roofline": None,
             "cpu_baseline": cpu,
             "clocks": clk,
-            "parity_sample": {"requests": len(keep), "ok": ok},
+            "parity_sample": {"requests": len(keep_idx), "arms": 3, "ok": ok},
         }
         print(json.dumps(line), flush=True)
 
@@ -906,7 +927,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--requests", type=int, default=2000, help="served: requests in the stream")
+    ap.add_argument("--requests", type=int, default=20000, help="served: requests in the stream")
     ap.add_argument("--pool", type=int, default=128, help="served: distinct pre-generated requests")
     ap.add_argument("--window", type=int, default=64, help="served: requests in flight (closed loop)")
     ap.add_argument("--streams", type=int, default=2, help="served: server compute streams")

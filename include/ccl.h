@@ -105,12 +105,20 @@ typedef enum {
                                   sites in increasing order (chains meet roots it already stored);
                                   0 the sites are interleaved over the warps (balances inputs
                                   without locality) */
-    CCL_OPT_ITER_CAP = 8       /* 0 (default): the loops of steps (ii)-(iv) stop only at caps
+    CCL_OPT_ITER_CAP = 8,      /* 0 (default): the loops of steps (ii)-(iv) stop only at caps
                                   derived from the input size, which a valid input never reaches.
                                   v > 0: a chase of step (ii)/(iv) gives up after v iterations and
                                   a warp of step (iii) abandons its window after v rounds, latching
                                   CCL_ERR_NONCONVERGED (ccl_sync); the labels are then incomplete.
                                   For testing the failure path; setting it drops cached graphs. */
+    CCL_OPT_REDUCE_WINDOW = 9, /* step (iii): most residual pairs a warp drains per window
+                                  (64..65536); 0 (default): 2048 when the call's labels fit in
+                                  three quarters of L2, else 512 */
+    CCL_OPT_ANALYSIS_GROUP = 10 /* steps (ii)/(iv) in contiguous order: G > 0 visits the sites in
+                                  super-chunks, every warp taking its next G groups of 64 sites
+                                  of each, so the labels in use stay in L2; 0 one range per
+                                  warp; -1 (default): 0 when the call's labels fit in three
+                                  quarters of L2, else 16 */
 } ccl_option;
 
 CCL_API ccl_status ccl_set_option(ccl_context *ctx, int option, int64_t value);

@@ -38,6 +38,8 @@ CCL_OPT_LINK_MODE = 5
 CCL_OPT_REFILL = 6
 CCL_OPT_ANALYSIS_ORDER = 7
 CCL_OPT_ITER_CAP = 8
+CCL_OPT_REDUCE_WINDOW = 9
+CCL_OPT_ANALYSIS_GROUP = 10
 
 
 class CclError(RuntimeError):

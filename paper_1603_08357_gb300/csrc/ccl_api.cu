@@ -31,6 +31,8 @@ struct TuneChoice {
     int link_mode = 0;
     int refill = 1;         // step (iii): 1 static per-lane pairs, 0 in-order hand-out
     int ana_seq = 1;        // steps (ii)/(iv): 1 contiguous ranges per warp, 0 interleaved
+    int red_window = 0;     // step (iii): most pairs per warp window; 0 by size (see resolve_tail)
+    int ana_group = -1;     // steps (ii)/(iv), contiguous order: super-chunk run length; -1 by size
 };
 
 struct GraphEntry {
@@ -57,6 +59,7 @@ struct GraphEntry {
 struct ccl_context {
     int device = 0;
     int num_sms = 0;
+    int64_t l2_bytes = 0;
     // workspace
     int2 *d_q = nullptr;
     int64_t q_cap = 0;
@@ -261,6 +264,27 @@ ccl_status tune_over(ccl_context *ctx, cudaStream_t s, const std::vector<TuneCho
     return st;
 }
 
+// Second tuning stage on the best first-stage choice: the step (iii) window,
+// then (contiguous order only) the step (ii)/(iv) super-chunk run length.
+template <typename Runner>
+ccl_status tune_tail(ccl_context *ctx, cudaStream_t s, int reps, TuneChoice &best, float &best_t, Runner runner) {
+    std::vector<TuneChoice> c;
+    for (int w : {256, 512, 1024, 2048}) {
+        TuneChoice t = best;
+        t.red_window = w;
+        c.push_back(t);
+    }
+    ccl_status st = tune_over(ctx, s, c, reps, best, best_t, runner);
+    if (st != CCL_OK || !best.ana_seq) return st;
+    c.clear();
+    for (int g : {0, 8, 16, 32}) {
+        TuneChoice t = best;
+        t.ana_group = g;
+        c.push_back(t);
+    }
+    return tune_over(ctx, s, c, reps, best, best_t, runner);
+}
+
 TuneChoice choice_for_class(ccl_context *ctx, int64_t cls) {
     auto it = ctx->tune_table.find(cls);
     if (it != ctx->tune_table.end()) return it->second;
@@ -307,9 +331,22 @@ ccl_status launch_init(const Params &P, bool batched, int64_t g, cudaStream_t s)
     return CCL_OK;
 }
 
+// The step (iii) window and the step (ii)/(iv) visiting order of a call:
+// explicit settings win; otherwise, when the call's labels fit in three
+// quarters of L2, long windows and one contiguous range per warp (every
+// gather hits L2 anyway), else windows of 512 pairs and super-chunks of 16
+// chunk groups per warp, so the labels the warps touch at once stay in L2.
+void resolve_tail(const ccl_context *ctx, const TuneChoice &tc, Params &P) {
+    const bool fits = 4 * kChunk * P.n_chunks <= ctx->l2_bytes * 3 / 4;
+    P.red_window = tc.red_window > 0 ? tc.red_window : (fits ? kRedWindowMax : 512);
+    P.ana_group = tc.ana_group >= 0 ? tc.ana_group : (fits ? 0 : 16);
+}
+
 // Steps (ii)-(iv) after step (i) has filled P.n_bands band records.
-ccl_status enqueue_tail(ccl_context *ctx, const Params &P, bool batched, const TuneChoice &tc, cudaStream_t s,
+ccl_status enqueue_tail(ccl_context *ctx, const Params &P0, bool batched, const TuneChoice &tc, cudaStream_t s,
                         bool profile) {
+    Params P = P0;
+    resolve_tail(ctx, tc, P);
     const int T = tc.threads;
     const int64_t warps_chunks = (P.n_chunks + kAnaChunks - 1) / kAnaChunks;
     const int64_t g_red = (int64_t)ctx->num_sms * blocks_per_sm(ctx, batched ? 5 : 4, 256);
@@ -368,7 +405,7 @@ uint64_t fnv1a(const void *data, size_t bytes, uint64_t h = 1469598103934665603u
 bool same_choice(const TuneChoice &a, const TuneChoice &b) {
     return a.threads == b.threads && a.ctas_per_sm == b.ctas_per_sm &&
            a.pre_analysis == b.pre_analysis && a.link_mode == b.link_mode && a.refill == b.refill &&
-           a.ana_seq == b.ana_seq;
+           a.ana_seq == b.ana_seq && a.red_window == b.red_window && a.ana_group == b.ana_group;
 }
 
 GraphEntry *find_graph(ccl_context *ctx, const GraphEntry &key) {
@@ -700,6 +737,9 @@ ccl_status ccl_context_create(ccl_context **out, int device) {
     ccl_context *ctx = new ccl_context();
     ctx->device = device;
     cudaError_t e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    int l2 = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device);
+    ctx->l2_bytes = l2;
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_band, kMaxBands * sizeof(BandRec));
@@ -734,11 +774,14 @@ ccl_status ccl_context_create(ccl_context **out, int device) {
             char line[256];
             while (fgets(line, sizeof line, f)) {     // a line that does not parse is skipped
                 long long cls;
-                int a, b, c, d, r, q;
-                if (sscanf(line, "%lld %d %d %d %d %d %d", &cls, &a, &b, &c, &d, &r, &q) != 7) continue;
+                int a, b, c, d, r, q, w = 0, g = -1;
+                const int nf = sscanf(line, "%lld %d %d %d %d %d %d %d %d", &cls, &a, &b, &c, &d, &r, &q, &w, &g);
+                if (nf != 7 && nf != 9) continue;
                 TuneChoice t;
                 t.threads = a; t.ctas_per_sm = b < 0 ? 0 : b; t.pre_analysis = c ? 1 : 0;
                 t.link_mode = d ? 1 : 0; t.refill = r ? 1 : 0; t.ana_seq = q ? 1 : 0;
+                t.red_window = (w >= 64 && w <= 65536) ? w : 0;
+                t.ana_group = g >= 0 ? g : -1;
                 if (t.threads >= 64 && t.threads <= 512 && t.threads % 32 == 0) ctx->tune_table[cls] = t;
             }
             fclose(f);
@@ -796,6 +839,14 @@ ccl_status ccl_set_option(ccl_context *ctx, int option, int64_t value) {
         case CCL_OPT_LINK_MODE: ctx->opt.link_mode = value ? 1 : 0; break;
         case CCL_OPT_REFILL: ctx->opt.refill = value ? 1 : 0; break;
         case CCL_OPT_ANALYSIS_ORDER: ctx->opt.ana_seq = value ? 1 : 0; break;
+        case CCL_OPT_REDUCE_WINDOW:
+            if (value != 0 && (value < 64 || value > 65536)) return CCL_ERR_INVALID_ARGUMENT;
+            ctx->opt.red_window = (int)value;
+            break;
+        case CCL_OPT_ANALYSIS_GROUP:
+            if (value < -1 || value > (int64_t)1 << 30) return CCL_ERR_INVALID_ARGUMENT;
+            ctx->opt.ana_group = (int)value;
+            break;
         case CCL_OPT_ITER_CAP:
             if (value < 0 || value > INT32_MAX) return CCL_ERR_INVALID_ARGUMENT;
             ctx->iter_cap = (int32_t)value;
@@ -823,6 +874,8 @@ ccl_status ccl_get_option(ccl_context *ctx, int option, int64_t *value) {
         case CCL_OPT_REFILL: *value = ctx->opt.refill; break;
         case CCL_OPT_ANALYSIS_ORDER: *value = ctx->opt.ana_seq; break;
         case CCL_OPT_ITER_CAP: *value = ctx->iter_cap; break;
+        case CCL_OPT_REDUCE_WINDOW: *value = ctx->opt.red_window; break;
+        case CCL_OPT_ANALYSIS_GROUP: *value = ctx->opt.ana_group; break;
         default: return CCL_ERR_INVALID_ARGUMENT;
     }
     return CCL_OK;
@@ -950,9 +1003,11 @@ ccl_status ccl_autotune_batched(ccl_context *ctx, int32_t K, const int64_t *site
                 }
     TuneChoice best = ctx->opt;
     float best_t = 1e30f;
-    ccl_status st = tune_over(ctx, s, cands, 3, best, best_t, [&](const TuneChoice &tc) {
+    auto runner = [&](const TuneChoice &tc) {
         return label_batched(ctx, K, site_off, ent_off, row_ptr, col_idx, bits, labels, stream, &tc);
-    });
+    };
+    ccl_status st = tune_over(ctx, s, cands, 3, best, best_t, runner);
+    if (st == CCL_OK) st = tune_tail(ctx, s, 3, best, best_t, runner);
     if (st != CCL_OK) return st;
     const int64_t n_tot = site_off[K], nnz_tot = ent_off[K];
     ctx->tune_table[batch_class(n_tot, nnz_tot, K)] = best;
@@ -1418,18 +1473,24 @@ ccl_status ccl_autotune(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t 
                         tc.refill = rf; tc.ana_seq = sq;
                         cands.push_back(tc);
                     }
-    st = tune_over(ctx, s, cands, 4, best, best_t, [&](const TuneChoice &tc) {
+    auto runner = [&](const TuneChoice &tc) {
         return label_single(ctx, n, nnz, row_ptr, col_idx, bits, labels, s, tc);
-    });
+    };
+    st = tune_over(ctx, s, cands, 4, best, best_t, runner);
+    if (st == CCL_OK) st = tune_tail(ctx, s, 4, best, best_t, runner);
     if (st != CCL_OK) return st;
     ctx->tune_table[size_class(n, nnz)] = best;
-    ctx->opt = best;     // also the default for other size classes
+    // also the default for other size classes, except the settings that
+    // follow the size of the call
+    ctx->opt = best;
+    ctx->opt.red_window = 0;
+    ctx->opt.ana_group = -1;
     if (const char *env = getenv("CCL_TUNE_CACHE")) {
         if (FILE *f = fopen(env, "w")) {
             for (auto &kv : ctx->tune_table)
-                fprintf(f, "%lld %d %d %d %d %d %d\n", (long long)kv.first, kv.second.threads,
+                fprintf(f, "%lld %d %d %d %d %d %d %d %d\n", (long long)kv.first, kv.second.threads,
                         kv.second.ctas_per_sm, kv.second.pre_analysis, kv.second.link_mode, kv.second.refill,
-                        kv.second.ana_seq);
+                        kv.second.ana_seq, kv.second.red_window, kv.second.ana_group);
             fclose(f);
         }
     }

@@ -498,10 +498,14 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
     unsigned long long my_pairs = 0;
     int64_t band_lo, band_hi;
     cta_band(P, band_lo, band_hi);
-    int64_t t_local = 0;
-    for (int64_t tile = band_lo; tile < band_hi; ++tile, ++t_local) {
-        const int s = (int)(t_local % kStages);
-        if (!mbar_wait_bounded(&full[s], (uint32_t)((t_local / kStages) & 1))) {
+    // stage s = tl % kStages and phase parity (tl / kStages) & 1 of local tile
+    // tl, kept incrementally in 32-bit (no 64-bit division per tile)
+    int s = 0;
+    uint32_t ph = 0;
+    const int32_t ntl = (int32_t)(band_hi - band_lo);
+    for (int32_t tl = 0; tl < ntl; ++tl, s = (s + 1 == kStages) ? 0 : s + 1, ph ^= (s == 0) ? 1u : 0u) {
+        const int64_t tile = band_lo + tl;
+        if (!mbar_wait_bounded(&full[s], ph)) {
             raise_err(P.err, kErrNonconv);
             break;
         }
@@ -566,24 +570,31 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
 // A warp walks kAnaChunks chunks at once (one chain per lane per chunk) so
 // that their dependent loads overlap.
 
-// kSeq = true: warp w walks a contiguous range of chunk groups in increasing
+// kSeq = true: warp w walks contiguous runs of chunk groups in increasing
 // order, so the chains of its later sites run into roots it has already
 // stored (lattices numbered row by row) and, batched, the instance of a chunk
-// changes rarely. kSeq = false: groups are interleaved over the warps (grid
-// stride), which balances inputs without locality (randomly numbered trees).
+// changes rarely. With P.ana_group = 0 each warp walks one range (the label
+// array fits in L2); with P.ana_group = G > 0 the groups are cut into
+// super-chunks of G groups per warp, all warps working inside one super-chunk
+// at a time, so the labels in use (and the roots their chains reach, in the
+// same instances) stay within L2 when the whole array does not fit.
+// kSeq = false: groups are interleaved over the warps (grid stride), which
+// balances inputs without locality (randomly numbered trees).
 template <bool kBatched, bool kSeq>
 __global__ void __launch_bounds__(512) k_analysis(Params P) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t ngroups = (P.n_chunks + kAnaChunks - 1) / kAnaChunks;
     const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int64_t per = kSeq ? (ngroups + nwarps - 1) / nwarps : 1;
-    const int64_t g0 = kSeq ? min(wid * per, ngroups) : wid;
-    const int64_t g1 = kSeq ? min(g0 + per, ngroups) : ngroups;
-    const int64_t gstep = kSeq ? 1 : nwarps;
+    const int64_t per = (ngroups + nwarps - 1) / nwarps;
+    // run length G and super-chunk stride: one run of `per` groups per warp,
+    // or runs of ana_group groups every nwarps * ana_group groups
+    const int64_t G = !kSeq ? 1 : (P.ana_group > 0 && P.ana_group < per ? (int64_t)P.ana_group : per);
+    const int64_t sc_stride = kSeq ? nwarps * G : nwarps;
     int kc = 0;                          // cached instance and its chunk range
     int64_t kc_lo = 0, kc_hi = kBatched ? 0 : P.n_chunks;
-    for (int64_t gidx = g0; gidx < g1; gidx += gstep) {
+    for (int64_t run = wid * G; run < ngroups; run += sc_stride)
+    for (int64_t gidx = run; gidx < min(run + G, ngroups); ++gidx) {
         int32_t *L[kAnaChunks];
         int32_t site[kAnaChunks], x[kAnaChunks], first[kAnaChunks];
         int32_t cap = 0;
@@ -697,8 +708,9 @@ __global__ void __launch_bounds__(256) k_reduce(Params P) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long wmax = P.red_window > 0 ? P.red_window : kRedWindowMax;
     long long win = (total + nwarps - 1) / nwarps;
-    win = win < 64 ? 64 : (win > kRedWindowMax ? kRedWindowMax : win);
+    win = win < 64 ? 64 : (win > wmax ? wmax : win);
     const long long nwin = (total + win - 1) / win;
 #ifdef CCL_DEVICE_STATS
     unsigned long long st_hops = 0, st_atom = 0, st_iter = 0;

@@ -35,7 +35,7 @@ constexpr int kAnaChunks = CCL_ANA_CHUNKS;
 #define CCL_RED_SLOTS 4
 #endif
 constexpr int kRedSlots = CCL_RED_SLOTS;
-constexpr int kRedWindowMax = 2048;   // pairs per warp window (fewer for small queues)
+constexpr int kRedWindowMax = 2048;   // default most pairs per warp window (fewer for small queues)
 constexpr int kMaxBands = 1024;
 
 // latched device error bits
@@ -88,6 +88,9 @@ struct Params {
     int64_t tile_off;          // step (i) on part of the tiles: its first tile ...
     int32_t band_off;          // ... and its first band record
     int32_t iter_cap;          // > 0: steps (ii)-(iv) give up after this many iterations (test option)
+    int32_t red_window;        // step (iii): most pairs per warp window (0: kRedWindowMax)
+    int32_t ana_group;         // steps (ii)/(iv), contiguous order: > 0 visit the sites in super-chunks
+                               // (every warp takes its next ana_group chunk groups of each), 0 one range per warp
     unsigned *err;
     unsigned long long *counters;   // [0] residual pairs
 };
