@@ -360,6 +360,7 @@ def run_ours(args, rank, world, local):
     # timed step with the oracle's labels of the same instance (rank 0, N=1)
     stats = ccl.ccl_get_stats(ctx)
     q = int(stats.residual_pairs)
+    opts.update(_settings(stats))
 
     # timed region: K steps, per-step CUDA events on the launching stream; the
     # library records events between its kernels (profiling ring) so that the
@@ -506,6 +507,13 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def _settings(stats) -> dict:
+    """The settings the library reports for its last call (tuned, set or
+    chosen by size)."""
+    return {k: int(getattr(stats, k)) for k in ("pre_analysis", "link_mode", "refill", "analysis_order",
+                                                 "reduce_window", "analysis_group", "analysis_park")}
+
+
 def _pin(arrays):
     """Page-locks host numpy arrays in place (cudaHostRegister through
     torch's runtime binding) so that copies from and to them run at the
@@ -563,9 +571,6 @@ def run_batched(args, rank, world, local):
         st_t, best_ms = ccl.ccl_autotune_batched(ctx, b.k, b.site_off, b.ent_off, rp, ci, bits, labels, stream)
         ccl.check(st_t, "ccl_autotune_batched")
         tuned = {"best_ms": best_ms}
-    opts = {name: ccl.ccl_get_option(ctx, o) for name, o in (
-        ("pre_analysis", ccl.CCL_OPT_PRE_ANALYSIS), ("link_mode", ccl.CCL_OPT_LINK_MODE),
-        ("refill", ccl.CCL_OPT_REFILL), ("analysis_order", ccl.CCL_OPT_ANALYSIS_ORDER))}
 
     def step():
         st = ccl.ccl_label_batched(ctx, b.k, b.site_off, b.ent_off, rp, ci, bits, labels, stream)
@@ -575,7 +580,9 @@ def run_batched(args, rank, world, local):
     for _ in range(max(args.warmup, 3)):
         step()
     ccl.check(ccl.ccl_sync(ctx, stream), "warm-up")
-    q = int(ccl.ccl_get_stats(ctx).residual_pairs)
+    stats = ccl.ccl_get_stats(ctx)
+    q = int(stats.residual_pairs)
+    opts = _settings(stats)
 
     # timed region: per-step CUDA events on the launching stream; the library
     # records events between its kernels for every timed step (profiling ring)

@@ -114,11 +114,16 @@ typedef enum {
     CCL_OPT_REDUCE_WINDOW = 9, /* step (iii): most residual pairs a warp drains per window
                                   (64..65536); 0 (default): 2048 when the call's labels fit in
                                   three quarters of L2, else 512 */
-    CCL_OPT_ANALYSIS_GROUP = 10 /* steps (ii)/(iv) in contiguous order: G > 0 visits the sites in
+    CCL_OPT_ANALYSIS_GROUP = 10, /* steps (ii)/(iv) in contiguous order: G > 0 visits the sites in
                                   super-chunks, every warp taking its next G groups of 64 sites
                                   of each, so the labels in use stay in L2; 0 one range per
                                   warp; -1 (default): 0 when the call's labels fit in three
                                   quarters of L2, else 16 */
+    CCL_OPT_ANALYSIS_PARK = 11 /* steps (ii)/(iv) in contiguous order: 1 chains still unfinished
+                                  after 4 rounds are set aside and finished 32 at a time, one per
+                                  lane; 0 every warp runs its longest chain to the end; -1
+                                  (default): 1 when the call's labels fit in three quarters of
+                                  L2, else 0 */
 } ccl_option;
 
 CCL_API ccl_status ccl_set_option(ccl_context *ctx, int option, int64_t value);
@@ -339,6 +344,11 @@ typedef struct {
        -DCCL_DEVICE_STATS (else 0): label loads of the root chases, atomicMin
        operations of the merge loops, warp iterations of the reduction */
     int64_t chase_loads, merge_atomics, reduce_iterations;
+    /* the settings the last call ran with (tuned, set, or chosen by size):
+       step (ii) on, step (iii) link mode and hand-out, step (ii)/(iv) order,
+       step (iii) window, step (ii)/(iv) super-chunk run length (0: one range
+       per warp), step (ii)/(iv) parking -- see ccl_option */
+    int32_t pre_analysis, link_mode, refill, analysis_order, reduce_window, analysis_group, analysis_park;
 } ccl_run_stats;
 
 /* Statistics of the context's last labelling call; waits for that call to

@@ -40,6 +40,7 @@ CCL_OPT_ANALYSIS_ORDER = 7
 CCL_OPT_ITER_CAP = 8
 CCL_OPT_REDUCE_WINDOW = 9
 CCL_OPT_ANALYSIS_GROUP = 10
+CCL_OPT_ANALYSIS_PARK = 11
 
 
 class CclError(RuntimeError):
@@ -53,7 +54,10 @@ class ccl_run_stats(ctypes.Structure):
     _fields_ = [("residual_pairs", ctypes.c_int64), ("n_sites", ctypes.c_int64),
                 ("nnz", ctypes.c_int64), ("n_inst", ctypes.c_int32), ("used_graph", ctypes.c_int32),
                 ("chase_loads", ctypes.c_int64), ("merge_atomics", ctypes.c_int64),
-                ("reduce_iterations", ctypes.c_int64)]
+                ("reduce_iterations", ctypes.c_int64), ("pre_analysis", ctypes.c_int32),
+                ("link_mode", ctypes.c_int32), ("refill", ctypes.c_int32), ("analysis_order", ctypes.c_int32),
+                ("reduce_window", ctypes.c_int32), ("analysis_group", ctypes.c_int32),
+                ("analysis_park", ctypes.c_int32)]
 
 
 class ccl_server_config(ctypes.Structure):

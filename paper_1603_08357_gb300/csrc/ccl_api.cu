@@ -33,6 +33,7 @@ struct TuneChoice {
     int ana_seq = 1;        // steps (ii)/(iv): 1 contiguous ranges per warp, 0 interleaved
     int red_window = 0;     // step (iii): most pairs per warp window; 0 by size (see resolve_tail)
     int ana_group = -1;     // steps (ii)/(iv), contiguous order: super-chunk run length; -1 by size
+    int ana_park = -1;      // steps (ii)/(iv), contiguous order: 1 park long chains, 0 not; -1 by size
 };
 
 struct GraphEntry {
@@ -159,6 +160,8 @@ int blocks_per_sm(ccl_context *ctx, int kernel_id, int threads) {
         case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init_dense<true>, kDenseThreads, 0); break;
         case 9: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init_dense_tma<false>, kInitThreads, kDenseSmem); break;
         case 10: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init_dense_tma<true>, kInitThreads, kDenseSmem); break;
+        case 11: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_analysis_park<false>, 32 * kParkWarps, 0); break;
+        case 12: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_analysis_park<true>, 32 * kParkWarps, 0); break;
         default: break;
     }
     if (e != cudaSuccess || nb < 1) { (void)cudaGetLastError(); nb = 1; }
@@ -282,6 +285,14 @@ ccl_status tune_tail(ccl_context *ctx, cudaStream_t s, int reps, TuneChoice &bes
         t.ana_group = g;
         c.push_back(t);
     }
+    st = tune_over(ctx, s, c, reps, best, best_t, runner);
+    if (st != CCL_OK) return st;
+    c.clear();
+    for (int k : {0, 1}) {
+        TuneChoice t = best;
+        t.ana_park = k;
+        c.push_back(t);
+    }
     return tune_over(ctx, s, c, reps, best, best_t, runner);
 }
 
@@ -336,10 +347,32 @@ ccl_status launch_init(const Params &P, bool batched, int64_t g, cudaStream_t s)
 // quarters of L2, long windows and one contiguous range per warp (every
 // gather hits L2 anyway), else windows of 512 pairs and super-chunks of 16
 // chunk groups per warp, so the labels the warps touch at once stay in L2.
+bool labels_fit_l2(const ccl_context *ctx, const Params &P) {
+    return 4 * kChunk * P.n_chunks <= ctx->l2_bytes * 3 / 4;
+}
+
 void resolve_tail(const ccl_context *ctx, const TuneChoice &tc, Params &P) {
-    const bool fits = 4 * kChunk * P.n_chunks <= ctx->l2_bytes * 3 / 4;
+    const bool fits = labels_fit_l2(ctx, P);
     P.red_window = tc.red_window > 0 ? tc.red_window : (fits ? kRedWindowMax : 512);
     P.ana_group = tc.ana_group >= 0 ? tc.ana_group : (fits ? 0 : 16);
+}
+
+// Parking of long chains in steps (ii)/(iv) (contiguous order only): explicit
+// setting, else on when the call's labels fit in three quarters of L2.
+bool resolve_park(const ccl_context *ctx, const TuneChoice &tc, const Params &P) {
+    if (!tc.ana_seq || P.iter_cap > 0) return false;    // the iteration-cap test option uses k_analysis
+    return tc.ana_park >= 0 ? tc.ana_park != 0 : labels_fit_l2(ctx, P);
+}
+
+// Records in the context's statistics the settings a call runs with.
+void note_settings(ccl_context *ctx, const TuneChoice &tc, const Params &P) {
+    ctx->last.pre_analysis = tc.pre_analysis;
+    ctx->last.link_mode = tc.link_mode;
+    ctx->last.refill = tc.refill;
+    ctx->last.analysis_order = tc.ana_seq;
+    ctx->last.reduce_window = P.red_window;
+    ctx->last.analysis_group = tc.ana_seq ? P.ana_group : 0;
+    ctx->last.analysis_park = resolve_park(ctx, tc, P) ? 1 : 0;
 }
 
 // Steps (ii)-(iv) after step (i) has filled P.n_bands band records.
@@ -347,11 +380,24 @@ ccl_status enqueue_tail(ccl_context *ctx, const Params &P0, bool batched, const 
                         bool profile) {
     Params P = P0;
     resolve_tail(ctx, tc, P);
+    note_settings(ctx, tc, P);
     const int T = tc.threads;
     const int64_t warps_chunks = (P.n_chunks + kAnaChunks - 1) / kAnaChunks;
     const int64_t g_red = (int64_t)ctx->num_sms * blocks_per_sm(ctx, batched ? 5 : 4, 256);
     if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[1], s));
+    const bool park = resolve_park(ctx, tc, P);
     auto analysis = [&]() {
+        if (park) {
+            // a full SM of warps (the kernel's registers and shared memory allow
+            // it; the occupancy query can assume a smaller shared-memory carveout)
+            const int64_t per_sm = std::max<int64_t>(blocks_per_sm(ctx, batched ? 12 : 11, 32 * kParkWarps),
+                                                     2048 / (32 * kParkWarps));
+            const int64_t need = (warps_chunks + kParkWarps - 1) / kParkWarps;
+            const unsigned gp = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * per_sm, need));
+            if (batched) k_analysis_park<true><<<gp, 32 * kParkWarps, 0, s>>>(P);
+            else k_analysis_park<false><<<gp, 32 * kParkWarps, 0, s>>>(P);
+            return;
+        }
         const unsigned g = (unsigned)grid_for(ctx, batched ? 3 : 2, tc, warps_chunks);
         if (batched) {
             if (tc.ana_seq) k_analysis<true, true><<<g, T, 0, s>>>(P);
@@ -405,7 +451,8 @@ uint64_t fnv1a(const void *data, size_t bytes, uint64_t h = 1469598103934665603u
 bool same_choice(const TuneChoice &a, const TuneChoice &b) {
     return a.threads == b.threads && a.ctas_per_sm == b.ctas_per_sm &&
            a.pre_analysis == b.pre_analysis && a.link_mode == b.link_mode && a.refill == b.refill &&
-           a.ana_seq == b.ana_seq && a.red_window == b.red_window && a.ana_group == b.ana_group;
+           a.ana_seq == b.ana_seq && a.red_window == b.red_window && a.ana_group == b.ana_group &&
+           a.ana_park == b.ana_park;
 }
 
 GraphEntry *find_graph(ccl_context *ctx, const GraphEntry &key) {
@@ -480,8 +527,8 @@ ccl_status upload_table(ccl_context *ctx, const std::vector<Inst> &table, cudaSt
 ccl_status run(ccl_context *ctx, Params P, bool batched, const TuneChoice &tc, cudaStream_t s,
                const std::vector<Inst> *table, uint64_t shape_hash, bool allow_graph = true,
                const std::vector<int64_t> *offsets = nullptr) {
-    for (int kid = 0; kid < 11; ++kid)
-        (void)blocks_per_sm(ctx, kid, kid >= 9 ? kInitThreads : kid >= 7 ? kDenseThreads
+    for (int kid = 0; kid < 13; ++kid)
+        (void)blocks_per_sm(ctx, kid, kid >= 11 ? 32 * kParkWarps : kid >= 9 ? kInitThreads : kid >= 7 ? kDenseThreads
                                                : (kid < 2 || kid == 6) ? kInitThreads : (kid >= 4 ? 256 : tc.threads));
     ctx->last.used_graph = 0;
     const bool capturing = stream_capturing(s);
@@ -536,6 +583,11 @@ ccl_status run(ccl_context *ctx, Params P, bool batched, const TuneChoice &tc, c
         g = &ctx->graphs.back();
     }
     g->last_use = ++ctx->use_clock;
+    {
+        Params R = P;
+        resolve_tail(ctx, tc, R);
+        note_settings(ctx, tc, R);
+    }
     CCL_CUDA(cudaGraphLaunch(g->exec, s));
     CCL_CUDA(cudaEventRecord(ctx->stats_ev, s));
     ctx->last.used_graph = 1;
@@ -774,14 +826,15 @@ ccl_status ccl_context_create(ccl_context **out, int device) {
             char line[256];
             while (fgets(line, sizeof line, f)) {     // a line that does not parse is skipped
                 long long cls;
-                int a, b, c, d, r, q, w = 0, g = -1;
-                const int nf = sscanf(line, "%lld %d %d %d %d %d %d %d %d", &cls, &a, &b, &c, &d, &r, &q, &w, &g);
-                if (nf != 7 && nf != 9) continue;
+                int a, b, c, d, r, q, w = 0, g = -1, k = -1;
+                const int nf = sscanf(line, "%lld %d %d %d %d %d %d %d %d %d", &cls, &a, &b, &c, &d, &r, &q, &w, &g, &k);
+                if (nf != 7 && nf != 10) continue;
                 TuneChoice t;
                 t.threads = a; t.ctas_per_sm = b < 0 ? 0 : b; t.pre_analysis = c ? 1 : 0;
                 t.link_mode = d ? 1 : 0; t.refill = r ? 1 : 0; t.ana_seq = q ? 1 : 0;
                 t.red_window = (w >= 64 && w <= 65536) ? w : 0;
                 t.ana_group = g >= 0 ? g : -1;
+                t.ana_park = k >= 0 ? (k ? 1 : 0) : -1;
                 if (t.threads >= 64 && t.threads <= 512 && t.threads % 32 == 0) ctx->tune_table[cls] = t;
             }
             fclose(f);
@@ -847,6 +900,10 @@ ccl_status ccl_set_option(ccl_context *ctx, int option, int64_t value) {
             if (value < -1 || value > (int64_t)1 << 30) return CCL_ERR_INVALID_ARGUMENT;
             ctx->opt.ana_group = (int)value;
             break;
+        case CCL_OPT_ANALYSIS_PARK:
+            if (value < -1 || value > 1) return CCL_ERR_INVALID_ARGUMENT;
+            ctx->opt.ana_park = (int)value;
+            break;
         case CCL_OPT_ITER_CAP:
             if (value < 0 || value > INT32_MAX) return CCL_ERR_INVALID_ARGUMENT;
             ctx->iter_cap = (int32_t)value;
@@ -876,6 +933,7 @@ ccl_status ccl_get_option(ccl_context *ctx, int option, int64_t *value) {
         case CCL_OPT_ITER_CAP: *value = ctx->iter_cap; break;
         case CCL_OPT_REDUCE_WINDOW: *value = ctx->opt.red_window; break;
         case CCL_OPT_ANALYSIS_GROUP: *value = ctx->opt.ana_group; break;
+        case CCL_OPT_ANALYSIS_PARK: *value = ctx->opt.ana_park; break;
         default: return CCL_ERR_INVALID_ARGUMENT;
     }
     return CCL_OK;
@@ -1485,12 +1543,13 @@ ccl_status ccl_autotune(ccl_context *ctx, int32_t n, int64_t nnz, const int32_t 
     ctx->opt = best;
     ctx->opt.red_window = 0;
     ctx->opt.ana_group = -1;
+    ctx->opt.ana_park = -1;
     if (const char *env = getenv("CCL_TUNE_CACHE")) {
         if (FILE *f = fopen(env, "w")) {
             for (auto &kv : ctx->tune_table)
-                fprintf(f, "%lld %d %d %d %d %d %d %d %d\n", (long long)kv.first, kv.second.threads,
+                fprintf(f, "%lld %d %d %d %d %d %d %d %d %d\n", (long long)kv.first, kv.second.threads,
                         kv.second.ctas_per_sm, kv.second.pre_analysis, kv.second.link_mode, kv.second.refill,
-                        kv.second.ana_seq, kv.second.red_window, kv.second.ana_group);
+                        kv.second.ana_seq, kv.second.red_window, kv.second.ana_group, kv.second.ana_park);
             fclose(f);
         }
     }

@@ -82,6 +82,26 @@ __device__ __forceinline__ Inst inst_of(const Params &P, int k) {
     return P.insts[k];
 }
 
+// The instance of a staged tile as the step (i) consumers use it: from the
+// kernel parameters for one instance, else from the stage header (shared
+// memory) that the producer filled from the instance table.
+template <bool kBatched>
+__device__ __forceinline__ Inst stage_inst(const Params &P, const StageHdr &h) {
+    if (!kBatched) return P.one;
+    Inst I;
+    I.row_ptr = h.i_rp;
+    I.col_idx = h.i_ci;
+    I.bits = h.i_bits;
+    I.labels = h.i_lab;
+    I.bit_off = h.i_bit_off;
+    I.tile_begin = h.i_tile_begin;
+    I.n = h.i_n;
+    I.nnz = h.i_nnz;
+    I.rp_lo = I.rp_hi = I.ci_lo = I.ci_hi = I.bits_lo = I.bits_hi = nullptr;   // not used by consumers
+    I.q_off = I.chunk_begin = 0;
+    return I;
+}
+
 // ---------------------------------------------------------------------------
 // mbarrier / bulk-copy primitives (inline PTX)
 
@@ -205,6 +225,14 @@ __device__ __forceinline__ void init_produce(const Params &P, Stage *st, uint64_
         h.e0 = __ldcs(I.row_ptr + h.s0);
         h.e1 = __ldcs(I.row_ptr + h.s0 + h.ts);
         h.status = (h.e0 < 0 || h.e1 < h.e0 || h.e1 > I.nnz) ? 1 : 0;
+        h.i_rp = I.row_ptr;
+        h.i_ci = I.col_idx;
+        h.i_bits = I.bits;
+        h.i_lab = I.labels;
+        h.i_bit_off = I.bit_off;
+        h.i_tile_begin = I.tile_begin;
+        h.i_n = I.n;
+        h.i_nnz = I.nnz;
         if (t_local == 0) {
             qband = I.q_off + (h.status ? 0 : h.e0);
             P.band[P.band_off + blockIdx.x].qbase = qband;
@@ -510,7 +538,7 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
             break;
         }
         const Stage &S = st[s];
-        const Inst I = inst_of<kBatched>(P, S.h.k);
+        const Inst I = stage_inst<kBatched>(P, S.h);
         if (lane == 0 && warp == 0) {
             // row_ptr[0] == 0 and row_ptr[n] == nnz, once per instance
             if (S.h.s0 == 0 && S.h.e0 != 0) raise_err(P.err, kErrShape);
@@ -646,6 +674,107 @@ __global__ void __launch_bounds__(512) k_analysis(Params P) {
         for (int u = 0; u < kAnaChunks; ++u)
             if (L[u] && x[u] != first[u] && site[u] < cap) L[u][site[u]] = x[u];
     }
+}
+
+// Steps (ii)/(iv) with parking, for inputs whose chains are mostly short but
+// have a long tail: every chain first gets kAnaRounds rounds in lockstep with
+// its warp (coalesced first loads, as k_analysis); the chains still
+// unfinished are appended to a per-warp list in shared memory and finished 32
+// at a time, one per lane, so a few long chains no longer hold up the lanes
+// of a whole group. Same visiting order (runs of P.ana_group groups, or one
+// range per warp) and the same results as k_analysis<kBatched, true>. (The
+// test option P.iter_cap is served by k_analysis alone.)
+constexpr int kAnaRounds = 4;
+constexpr int kParkWarps = 8;                        // warps per CTA (256 threads)
+constexpr int kParkCap = 32 * kAnaChunks + 32;       // < 32 left + one group's chains
+template <bool kBatched>
+__global__ void __launch_bounds__(256) k_analysis_park(Params P) {
+    __shared__ int s_site[8][kParkCap];
+    __shared__ int s_x[8][kParkCap];
+    __shared__ int s_k[kBatched ? 8 : 1][kBatched ? kParkCap : 1];
+    const int lane = threadIdx.x & 31;
+    const int wl = threadIdx.x >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t ngroups = (P.n_chunks + kAnaChunks - 1) / kAnaChunks;
+    const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + wl;
+    const int64_t per = (ngroups + nwarps - 1) / nwarps;
+    const int64_t G = (P.ana_group > 0 && P.ana_group < per ? (int64_t)P.ana_group : per);
+    const int64_t sc_stride = nwarps * G;
+    int kc = 0;
+    int64_t kc_lo = 0, kc_hi = kBatched ? 0 : P.n_chunks;
+    int cnt = 0;
+    const unsigned lt = (1u << lane) - 1u;
+    const int32_t capit = (int32_t)min(32 * P.n_chunks, (int64_t)INT32_MAX - 1);
+    auto drain = [&](int take) {
+        const int base = cnt - take;
+        const bool act0 = lane < take;
+        int site = 0, x = 0;
+        int32_t *Lp = P.one.labels;
+        if (act0) {
+            site = s_site[wl][base + lane];
+            x = s_x[wl][base + lane];
+            if (kBatched) Lp = P.insts[s_k[wl][base + lane]].labels;
+        }
+        bool act = act0;
+        for (int32_t it = 0;; ++it) {
+            const int32_t y = act ? Lp[x] : 0;
+            if (act) { if (y == x) act = false; else x = y; }
+            if (!__any_sync(kFull, act)) break;
+            if (it > capit || (P.iter_cap > 0 && it + 1 + kAnaRounds >= P.iter_cap)) { raise_err(P.err, kErrNonconv); break; }
+        }
+        if (act0) Lp[site] = x;
+        cnt = base;
+        __syncwarp();
+    };
+    for (int64_t run = wid * G; run < ngroups; run += sc_stride)
+    for (int64_t gidx = run; gidx < min(run + G, ngroups); ++gidx) {
+        int32_t *L[kAnaChunks];
+        int32_t site[kAnaChunks], x[kAnaChunks], first[kAnaChunks];
+        int kk[kAnaChunks];
+        bool act[kAnaChunks];
+#pragma unroll
+        for (int u = 0; u < kAnaChunks; ++u) {
+            const int64_t c = gidx * kAnaChunks + u;
+            act[u] = false; L[u] = nullptr; site[u] = 0; kk[u] = 0;
+            if (c < P.n_chunks) {
+                if (kBatched && (c < kc_lo || c >= kc_hi)) {
+                    kc = find_inst(P, c);
+                    kc_lo = P.insts[kc].chunk_begin;
+                    kc_hi = kc + 1 < P.K ? P.insts[kc + 1].chunk_begin : P.n_chunks;
+                }
+                const Inst I = inst_of<kBatched>(P, kc);
+                site[u] = (int32_t)((c - I.chunk_begin) * kChunk) + lane;
+                L[u] = I.labels; kk[u] = kc;
+                act[u] = site[u] < I.n;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kAnaChunks; ++u) x[u] = act[u] ? L[u][site[u]] : 0;
+#pragma unroll
+        for (int u = 0; u < kAnaChunks; ++u) { first[u] = x[u]; act[u] = act[u] && x[u] != site[u]; }
+#pragma unroll
+        for (int r = 0; r < kAnaRounds; ++r) {
+            int32_t y[kAnaChunks];
+#pragma unroll
+            for (int u = 0; u < kAnaChunks; ++u) y[u] = act[u] ? L[u][x[u]] : 0;
+#pragma unroll
+            for (int u = 0; u < kAnaChunks; ++u)
+                if (act[u]) { if (y[u] == x[u]) act[u] = false; else x[u] = y[u]; }
+        }
+#pragma unroll
+        for (int u = 0; u < kAnaChunks; ++u) {
+            if (!act[u] && L[u] && x[u] != first[u]) L[u][site[u]] = x[u];
+            const unsigned pk = __ballot_sync(kFull, act[u]);
+            if (pk) {
+                const int pos = cnt + __popc(pk & lt);
+                if (act[u]) { s_site[wl][pos] = site[u]; s_x[wl][pos] = x[u]; if (kBatched) s_k[wl][pos] = kk[u]; }
+                cnt += __popc(pk);
+                __syncwarp();
+                if (cnt >= 32) drain(32);
+            }
+        }
+    }
+    while (cnt > 0) drain(min(cnt, 32));
 }
 
 // ---------------------------------------------------------------------------

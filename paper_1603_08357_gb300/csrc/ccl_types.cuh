@@ -104,6 +104,13 @@ struct __align__(16) StageHdr {
     int32_t status;            // 0 valid, 1 corrupt row pointers
     int32_t pad_;
     int64_t qband;             // first queue slot of this CTA's band
+    // the fields of the tile's instance the consumers use (batched calls read
+    // them here instead of from the instance table in global memory)
+    const int32_t *i_rp, *i_ci;
+    const uint32_t *i_bits;
+    int32_t *i_lab;
+    int64_t i_bit_off, i_tile_begin;
+    int32_t i_n, i_nnz;
 };
 
 struct __align__(16) Stage {

@@ -320,21 +320,27 @@ def test_batched_host_path_large_groups(ctx):
     assert np.array_equal(out, oracle.uf_label_batched(b))
 
 
-@pytest.mark.parametrize("window,group", [(64, 0), (512, 16), (2048, 1), (65536, 3)])
-def test_window_and_super_chunk_settings_same_labels(window, group):
-    """Every step-(iii) window length and step-(ii)/(iv) super-chunk run
-    length gives the oracle's labels, single and batched (the run length
-    splits instances across super-chunks), with step (ii) on."""
+@pytest.mark.parametrize("window,group,park", [(64, 0, 0), (512, 16, 1), (2048, 1, 1), (65536, 3, 0),
+                                               (1024, 0, 1)])
+def test_window_and_super_chunk_settings_same_labels(window, group, park):
+    """Every step-(iii) window length, step-(ii)/(iv) super-chunk run length
+    and parking setting gives the oracle's labels, single and batched (the
+    run length splits instances across super-chunks), with step (ii) on;
+    the statistics report the settings used."""
     lat = L.triangle(700, L.PC_TRIANGLE, 12)
-    b = L.make_batch(_mixed_specs(60, 13) + [dict(kind="honeycomb", L=400, p=L.PC_HONEYCOMB, seed=3)])
+    b = L.make_batch(_mixed_specs(60, 13) + [dict(kind="honeycomb", L=400, p=L.PC_HONEYCOMB, seed=3),
+                                             dict(kind="cayley", z=3, shells=15, p=0.5, seed=4, perm_seed=4)])
     c = ccl.ccl_context_create(0)
     try:
         for opt, v in ((ccl.CCL_OPT_REDUCE_WINDOW, window), (ccl.CCL_OPT_ANALYSIS_GROUP, group),
-                       (ccl.CCL_OPT_PRE_ANALYSIS, 1)):
+                       (ccl.CCL_OPT_ANALYSIS_PARK, park), (ccl.CCL_OPT_PRE_ANALYSIS, 1)):
             assert ccl.ccl_set_option(c, opt, v) == ccl.CCL_OK
             assert ccl.ccl_get_option(c, opt) == v
         assert np.array_equal(gpu_label(c, lat), oracle.uf_label(lat))
+        st = ccl.ccl_get_stats(c)
+        assert (st.reduce_window, st.analysis_group, st.analysis_park, st.pre_analysis) == (window, group, park, 1)
         assert np.array_equal(gpu_label_batched(c, b), oracle.uf_label_batched(b))
+        assert ccl.ccl_set_option(c, ccl.CCL_OPT_ANALYSIS_PARK, 2) == ccl.CCL_ERR_INVALID_ARGUMENT
         assert ccl.ccl_set_option(c, ccl.CCL_OPT_REDUCE_WINDOW, 63) == ccl.CCL_ERR_INVALID_ARGUMENT
         assert ccl.ccl_set_option(c, ccl.CCL_OPT_ANALYSIS_GROUP, -2) == ccl.CCL_ERR_INVALID_ARGUMENT
     finally:
@@ -513,9 +519,10 @@ def test_tune_cache_file_roundtrip(tmp_path, monkeypatch):
     finally:
         ccl.ccl_context_destroy(c)
     rows = [list(map(int, l.split())) for l in path.read_text().splitlines() if l.strip()]
-    assert len(rows) >= 1 and all(len(r) == 9 for r in rows)
+    assert len(rows) >= 1 and all(len(r) == 10 for r in rows)
     assert all(r[1] in (128, 256, 512) and r[3] in (0, 1) and r[4] in (0, 1) for r in rows)
-    assert all(r[7] in (0, 256, 512, 1024, 2048) and r[8] in (-1, 0, 8, 16, 32) for r in rows)
+    assert all(r[7] in (0, 256, 512, 1024, 2048) and r[8] in (-1, 0, 8, 16, 32) and r[9] in (-1, 0, 1)
+               for r in rows)
     # a new context reads the table back (and the older 7-field lines);
     # malformed lines are skipped
     old_form = " ".join(map(str, rows[0][:7]))
