@@ -63,7 +63,8 @@ def test_committed_traffic_is_plausible():
     small factor of the bytes its workload holds (a unit slip in turning ncu's
     Mbyte/Gbyte columns into bytes moves it by 10^3)."""
     sizes = {"tri4096": (4096 * 4096, 6 * 4096 * 4096), "tri4096/dense": (4096 * 4096, 6 * 4096 * 4096),
-             "bethe24": (1 + 3 * (2 ** 24 - 1), 2 * 3 * (2 ** 24 - 1))}
+             "bethe24": (1 + 3 * (2 ** 24 - 1), 2 * 3 * (2 ** 24 - 1)),
+             "batched": (2_127_258_178, 7_325_653_934)}
     with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
         traffic = json.load(fh)
     assert traffic
