@@ -672,8 +672,11 @@ def run_batched(args, rank, world, local):
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
+    e_step_ms = []
     for _ in range(e_steps):
+        t1 = time.perf_counter()
         e2e_step()
+        e_step_ms.append(1e3 * (time.perf_counter() - t1))
     e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / e_steps, dist, dev)
     unpin()
     e2e_same = bool(np.array_equal(h_lab, got))
@@ -725,6 +728,7 @@ def run_batched(args, rank, world, local):
             "cpu_baseline": cpu,
             "e2e": {"value": world * b.n_total / (e_ms / 1e3), "unit": "sites/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e_ms,
+                    "step_ms": [round(x, 2) for x in e_step_ms],
                     "entry": "ccl_label_batched_host (page-locked host arrays)",
                     "labels_identical": e2e_same},
             "gpu_launches": args.steps * (4 if opts["pre_analysis"] else 3),

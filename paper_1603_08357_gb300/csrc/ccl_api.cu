@@ -92,6 +92,7 @@ struct ccl_context {
     int use_graphs = 1;
     int profile = 0;
     int32_t iter_cap = 0;       // CCL_OPT_ITER_CAP
+    double ws_growth = 1.0;     // a growing workspace takes max(need, ws_growth * current) slots
     std::map<int64_t, TuneChoice> tune_table;
     // graphs
     std::vector<GraphEntry> graphs;
@@ -200,21 +201,30 @@ void drop_graphs(ccl_context *ctx) {
 // more), plus the per-pair instance for batched calls.
 ccl_status ensure_workspace(ccl_context *ctx, int64_t q_slots, bool batched) {
     if (q_slots > ctx->q_cap || (batched && q_slots > ctx->qk_cap)) drop_graphs(ctx);  // graphs hold the pointers
+    // a grown allocation of `want` elements (at least `need`), or of exactly
+    // `need` when the larger one does not fit
+    auto grow = [](void **p, int64_t &cap, int64_t need, int64_t want, size_t elem) {
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+        cap = 0;
+        cudaError_t e = cudaMalloc(p, (size_t)want * elem);
+        if (e == cudaErrorMemoryAllocation && want > need) {
+            (void)cudaGetLastError();
+            want = need;
+            e = cudaMalloc(p, (size_t)want * elem);
+        }
+        if (e == cudaSuccess) cap = want;
+        return e;
+    };
     if (q_slots > ctx->q_cap) {
-        if (ctx->d_q) cudaFree(ctx->d_q);
-        ctx->d_q = nullptr;
-        ctx->q_cap = 0;
-        const int64_t want = std::max<int64_t>(q_slots, 1024);
-        CCL_CUDA(cudaMalloc(&ctx->d_q, (size_t)want * sizeof(int2)));
-        ctx->q_cap = want;
+        const int64_t need = std::max<int64_t>(q_slots, 1024);
+        const int64_t want = std::max<int64_t>(need, (int64_t)(ctx->ws_growth * (double)ctx->q_cap));
+        CCL_CUDA(grow((void **)&ctx->d_q, ctx->q_cap, need, want, sizeof(int2)));
     }
     if (batched && q_slots > ctx->qk_cap) {
-        if (ctx->d_qk) cudaFree(ctx->d_qk);
-        ctx->d_qk = nullptr;
-        ctx->qk_cap = 0;
-        const int64_t want = std::max<int64_t>(q_slots, 1024);
-        CCL_CUDA(cudaMalloc(&ctx->d_qk, (size_t)want * sizeof(int32_t)));
-        ctx->qk_cap = want;
+        const int64_t need = std::max<int64_t>(q_slots, 1024);
+        const int64_t want = std::max<int64_t>(need, (int64_t)(ctx->ws_growth * (double)ctx->qk_cap));
+        CCL_CUDA(grow((void **)&ctx->d_qk, ctx->qk_cap, need, want, sizeof(int32_t)));
     }
     return CCL_OK;
 }
@@ -502,19 +512,22 @@ bool stream_capturing(cudaStream_t s) {
 // staging buffer, after the previous upload has left that buffer.
 ccl_status upload_table(ccl_context *ctx, const std::vector<Inst> &table, cudaStream_t s) {
     const int64_t K = (int64_t)table.size();
+    // tables grow at least twofold (each growth synchronises the device)
     if (K > ctx->h_insts_cap) {
+        const int64_t want = std::max<int64_t>({K, 64, 2 * ctx->h_insts_cap});
         if (ctx->h_insts) { cudaEventSynchronize(ctx->staging_free); cudaFreeHost(ctx->h_insts); }
         ctx->h_insts = nullptr;
         ctx->h_insts_cap = 0;
-        CCL_CUDA(cudaMallocHost(&ctx->h_insts, (size_t)K * sizeof(Inst)));
-        ctx->h_insts_cap = K;
+        CCL_CUDA(cudaMallocHost(&ctx->h_insts, (size_t)want * sizeof(Inst)));
+        ctx->h_insts_cap = want;
     }
     if (K > ctx->insts_cap) {
+        const int64_t want = std::max<int64_t>({K, 64, 2 * ctx->insts_cap});
         if (ctx->d_insts) cudaFree(ctx->d_insts);
         ctx->d_insts = nullptr;
         ctx->insts_cap = 0;
-        CCL_CUDA(cudaMalloc(&ctx->d_insts, (size_t)K * sizeof(Inst)));
-        ctx->insts_cap = K;
+        CCL_CUDA(cudaMalloc(&ctx->d_insts, (size_t)want * sizeof(Inst)));
+        ctx->insts_cap = want;
     }
     CCL_CUDA(cudaEventSynchronize(ctx->staging_free));
     memcpy(ctx->h_insts, table.data(), (size_t)K * sizeof(Inst));
@@ -740,6 +753,12 @@ ccl_status label_instances(ccl_context *ctx, std::vector<Inst> &table, cudaStrea
 // the largest call and is kept until released).
 int64_t workspace_bytes(const ccl_context *ctx) {
     return ctx->q_cap * (int64_t)sizeof(int2) + ctx->qk_cap * (int64_t)sizeof(int32_t);
+}
+
+// Growth factor of the residual-pair workspace: a call that needs more slots
+// than the context holds takes max(need, factor * held) (1 = exactly the need).
+void set_workspace_growth(ccl_context *ctx, double factor) {
+    ctx->ws_growth = factor < 1.0 ? 1.0 : factor;
 }
 
 // Frees the residual-pair workspace (and the graphs that point into it); the

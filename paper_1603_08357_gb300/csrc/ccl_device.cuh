@@ -253,6 +253,17 @@ __device__ __forceinline__ void init_produce(const Params &P, Stage *st, uint64_
             h.ci_lo = h.ci_hi = 0;
             h.w_lo = h.w_hi = 0;
         }
+        h.t_rb0 = (int32_t)(I.bit_off - (h.w_lo << 5));
+        h.t_nbits = (int32_t)(32 * (h.w_hi - h.w_lo));
+        h.t_staged = h.status == 0 && h.e0 >= h.ci_lo && h.e1 <= h.ci_hi &&
+                     (kGen || (h.t_rb0 + h.e0 >= 0 && h.t_rb0 + h.e1 <= h.t_nbits));
+        {
+            // tiles of this band finished at least kStages tiles ago
+            const int64_t lo = max(band_lo, I.tile_begin) - I.tile_begin;
+            const int64_t hi = tile - kStages - I.tile_begin;
+            h.t_vis_lo = (int32_t)lo;
+            h.t_vis_hi = hi < lo ? -1 : (int32_t)hi;
+        }
         st[s].h = h;
         const uint32_t b_rp = 4u * (uint32_t)(h.rp_hi - h.rp_lo);
         const uint32_t b_ci = 4u * (uint32_t)(h.ci_hi - h.ci_lo);
@@ -545,16 +556,11 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
             if (S.h.s0 + S.h.ts == I.n && S.h.e1 != I.nnz) raise_err(P.err, kErrShape);
         }
         TileCtx tc;
-        tc.rb0 = (int32_t)(I.bit_off - (S.h.w_lo << 5));
-        tc.nbits = (int32_t)(32 * (S.h.w_hi - S.h.w_lo));
-        tc.staged = S.h.status == 0 && S.h.e0 >= S.h.ci_lo && S.h.e1 <= S.h.ci_hi &&
-                    (kGen || (tc.rb0 + S.h.e0 >= 0 && tc.rb0 + S.h.e1 <= tc.nbits));
-        {
-            const int64_t lo = max(band_lo, I.tile_begin) - I.tile_begin;
-            const int64_t hi = tile - kStages - I.tile_begin;
-            tc.vis_lo = (int32_t)lo;
-            tc.vis_hi = hi < lo ? -1 : (int32_t)hi;
-        }
+        tc.rb0 = S.h.t_rb0;
+        tc.nbits = S.h.t_nbits;
+        tc.staged = S.h.t_staged != 0;
+        tc.vis_lo = S.h.t_vis_lo;
+        tc.vis_hi = S.h.t_vis_hi;
         static_assert(kChunksPerConsumer == 2, "a consumer warp scans two chunks per tile");
         {
             // both chunks are scanned first; their pairs then take one range of

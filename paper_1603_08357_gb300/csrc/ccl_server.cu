@@ -39,6 +39,7 @@ namespace ccl {
 ccl_status label_instances(ccl_context *ctx, std::vector<Inst> &table, cudaStream_t s);
 int64_t workspace_bytes(const ccl_context *ctx);
 void release_workspace(ccl_context *ctx);
+void set_workspace_growth(ccl_context *ctx, double factor);
 }
 
 namespace {
@@ -595,6 +596,10 @@ ccl_status ccl_server_create(ccl_server **out, const ccl_server_config *cfg_in) 
         ccl_context *c = nullptr;
         if (ccl_context_create(&c, cfg.device) != CCL_OK) { e = cudaErrorUnknown; break; }
         ccl_set_option(c, CCL_OPT_USE_GRAPHS, 0);
+        // batches of varying size: grow the workspace twofold, so it is
+        // reallocated (a device-wide synchronisation) a few times, not at
+        // every new largest batch
+        ccl::set_workspace_growth(c, 2.0);
         S->ctxs.push_back(c);
     }
     if (e != cudaSuccess) {

@@ -111,6 +111,11 @@ struct __align__(16) StageHdr {
     int32_t *i_lab;
     int64_t i_bit_off, i_tile_begin;
     int32_t i_n, i_nnz;
+    // per-tile values every consumer warp needs, computed once by the producer:
+    // stage-relative bit index of local entry 0, bits present, whether the
+    // stage holds the tile's whole entry range, and the instance-local tiles
+    // [vis_lo, vis_hi] of the band whose labels are final and visible
+    int32_t t_rb0, t_nbits, t_staged, t_vis_lo, t_vis_hi, pad2_;
 };
 
 struct __align__(16) Stage {
