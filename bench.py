@@ -507,6 +507,12 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def _phases(st) -> dict:
+    """The request loop's latency by phase (p50 / p99 in ms)."""
+    names = ("admit", "upload", "wait_launch", "gpu_and_return")
+    return {n: [round(st.phase_p50_ms[k], 3), round(st.phase_p99_ms[k], 3)] for k, n in enumerate(names)}
+
+
 def _settings(stats) -> dict:
     """The settings the library reports for its last call (tuned, set or
     chosen by size)."""
@@ -780,10 +786,39 @@ def run_served(args, rank, world, local):
     submit = submit_with(ccl.ccl_server_submit, "ccl_server_submit")
 
     def new_server():
-        srv = ccl.ccl_server_create(local, n_streams=args.streams, max_batch=1024, host_staging_bytes=4 << 30)
+        srv = ccl.ccl_server_create(local, n_streams=args.streams, max_batch=1024, host_staging_bytes=8 << 30)
         for lat in pool[:16]:                                   # warm-up
             ccl.check(ccl.ccl_server_wait(srv, submit_nocopy(srv, lat), out_bufs[id(lat)], 600_000), "warm-up")
         return srv
+
+    def collect(srv, tickets, keep=None, sem=None):
+        """Waits for every ticket with args.waiters client threads (thread t
+        takes requests t, t + waiters, ... in order), as a serving front end
+        with several connections would; labels of the kept requests go to
+        buffers of their own."""
+        errors = []
+
+        def waiter(t):
+            try:
+                for k in range(t, len(req), args.waiters):
+                    while tickets[k] is None:
+                        time.sleep(0.00005)
+                    lat = req[k]
+                    buf = np.empty(lat.n, np.int32) if keep is not None and k in keep_idx else out_bufs[id(lat)]
+                    ccl.check(ccl.ccl_server_wait(srv, tickets[k], buf, 600_000), "ccl_server_wait")
+                    if keep is not None and k in keep_idx:
+                        keep[k] = buf
+                    if sem is not None:
+                        sem.release()
+            except Exception as e:          # reported by the main thread
+                errors.append(e)
+        ths = [threading.Thread(target=waiter, args=(t,)) for t in range(args.waiters)]
+        for th in ths:
+            th.start()
+        for th in ths:
+            th.join()
+        if errors:
+            raise errors[0]
 
     def closed_loop(sub):
         srv = new_server()
@@ -799,14 +834,7 @@ def run_served(args, rank, world, local):
         t0 = time.perf_counter()
         th = threading.Thread(target=feeder)
         th.start()
-        for k, lat in enumerate(req):
-            while tickets[k] is None:
-                time.sleep(0.00005)
-            buf = np.empty(lat.n, np.int32) if k in keep_idx else out_bufs[id(lat)]
-            ccl.check(ccl.ccl_server_wait(srv, tickets[k], buf, 600_000), "ccl_server_wait")
-            if k in keep_idx:
-                keep[k] = buf
-            sem.release()
+        collect(srv, tickets, keep, sem)
         th.join()
         wall = time.perf_counter() - t0
         st = ccl.ccl_server_stats_get(srv)
@@ -860,10 +888,7 @@ def run_served(args, rank, world, local):
         t1 = time.perf_counter()
         th = threading.Thread(target=open_feeder)
         th.start()
-        for k, lat in enumerate(req):
-            while tk[k] is None:
-                time.sleep(0.00005)
-            ccl.check(ccl.ccl_server_wait(srv, tk[k], out_bufs[id(lat)], 600_000), "ccl_server_wait")
+        collect(srv, tk)
         th.join()
         el = time.perf_counter() - t1
         so = ccl.ccl_server_stats_get(srv)
@@ -871,7 +896,8 @@ def run_served(args, rank, world, local):
         # the server's percentiles cover the 16 warm-up requests too (tiny next to the stream)
         loads[str(load)] = {"offered_req_per_s": rate, "achieved_sites_per_s": total_sites / el,
                             "p50_ms": so.p50_ms, "p99_ms": so.p99_ms, "max_ms": so.max_ms,
-                            "batches": int(so.batches)}
+                            "batches": int(so.batches), "arena_misses": int(so.arena_misses),
+                            "phases": _phases(so)}
     unpin()
 
     ok = None
@@ -899,14 +925,17 @@ def run_served(args, rank, world, local):
             "data": "synthetic",
             "config": {"workload": "served", "requests": len(req), "pool": len(pool),
                        "mean_sites": mean_sites, "window": args.window, "streams": args.streams,
+                       "client_waiters": args.waiters,
                        "generation_s": t_gen, "host_arrays": "page-locked",
                        "l2": "inputs larger than L2 in aggregate (no flush)"},
             "closed_loop": {"submit": "ccl_server_submit_nocopy", "wall_s": wall,
                             "requests_per_s": len(req) / wall, "batches": int(st_closed.batches),
-                            "p50_ms": st_closed.p50_ms, "p99_ms": st_closed.p99_ms},
+                            "p50_ms": st_closed.p50_ms, "p99_ms": st_closed.p99_ms,
+                            "arena_misses": int(st_closed.arena_misses), "phases": _phases(st_closed)},
             "closed_loop_copying": {"submit": "ccl_server_submit", "sites_per_s": total_sites / wall_copy,
                                     "requests_per_s": len(req) / wall_copy, "batches": int(st_copy.batches),
-                                    "p50_ms": st_copy.p50_ms, "p99_ms": st_copy.p99_ms},
+                                    "p50_ms": st_copy.p50_ms, "p99_ms": st_copy.p99_ms,
+                                    "arena_misses": int(st_copy.arena_misses), "phases": _phases(st_copy)},
             "one_at_a_time": {"entry": "ccl_label_host, one call per request, same host arrays",
                               "value": world * total_sites / wall_one, "unit": "sites/s", "wall_s": wall_one,
                               "requests_per_s": len(req) / wall_one,
@@ -942,6 +971,7 @@ def main():
     ap.add_argument("--pool", type=int, default=128, help="served: distinct pre-generated requests")
     ap.add_argument("--window", type=int, default=64, help="served: requests in flight (closed loop)")
     ap.add_argument("--streams", type=int, default=2, help="served: server compute streams")
+    ap.add_argument("--waiters", type=int, default=4, help="served: client threads collecting results")
     ap.add_argument("--loads", type=float, nargs="*", default=[0.5, 0.8],
                     help="served: open-loop arrival rates as fractions of the capacity")
     ap.add_argument("--input", choices=["csr", "dense", "random", "dense-random"], default="csr",

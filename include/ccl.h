@@ -447,6 +447,13 @@ typedef struct {
     double busy_seconds;             /* wall time from first submit to last completion */
     double sites_per_second;
     int64_t waiting;                 /* threads inside ccl_server_wait now */
+    int64_t arena_misses;            /* requests whose host copy (ccl_server_submit) or labels
+                                        (ccl_server_submit_nocopy) did not fit the pinned staging
+                                        arena and went through pageable memory */
+    /* latency by phase, p50 and p99 over completed requests:
+       [0] submit -> admitted (upload started), [1] -> upload seen complete,
+       [2] -> launched in a batch, [3] -> labels on host */
+    double phase_p50_ms[4], phase_p99_ms[4];
 } ccl_server_stats;
 
 /* Starts the server thread. cfg may be NULL for defaults. */

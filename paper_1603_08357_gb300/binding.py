@@ -79,7 +79,8 @@ class ccl_server_stats(ctypes.Structure):
                 ("sites_completed", ctypes.c_int64), ("p50_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
                 ("busy_seconds", ctypes.c_double), ("sites_per_second", ctypes.c_double),
-                ("waiting", ctypes.c_int64)]
+                ("waiting", ctypes.c_int64), ("arena_misses", ctypes.c_int64),
+                ("phase_p50_ms", ctypes.c_double * 4), ("phase_p99_ms", ctypes.c_double * 4)]
 
 
 def _load() -> ctypes.CDLL:

@@ -1235,9 +1235,15 @@ ccl_status ccl_sync(ccl_context *ctx, void *stream, int64_t timeout_ms) {
         }
         if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
+    // the error word is read (and cleared) on the context's own non-blocking
+    // stream, so the read waits for nothing else on the device
     unsigned err = 0;
-    CCL_CUDA(cudaMemcpy(&err, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
-    if (err) CCL_CUDA(cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
+    CCL_CUDA(cudaMemcpyAsync(&err, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->cap_stream));
+    CCL_CUDA(cudaStreamSynchronize(ctx->cap_stream));
+    if (err) {
+        CCL_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->cap_stream));
+        CCL_CUDA(cudaStreamSynchronize(ctx->cap_stream));
+    }
     if (err & kErrIndex) return CCL_ERR_INDEX_OUT_OF_RANGE;
     if (err & kErrShape) return CCL_ERR_INVALID_ARGUMENT;
     if (err & kErrNonconv) return CCL_ERR_NONCONVERGED;

@@ -73,6 +73,7 @@ struct Req {
     char *d_mem = nullptr;
     cudaEvent_t uploaded = nullptr;
     Clock::time_point t_submit, t_done;
+    Clock::time_point t_admit, t_ready, t_launch;   // upload started, upload seen done, batch launched
     ccl_status status = CCL_OK;
     bool done = false;
     bool dropped = false;   // ended by ccl_server_destroy before it was labelled
@@ -255,8 +256,9 @@ struct ccl_server {
     std::vector<Batch> inflight;
 
     // statistics (under mu)
-    int64_t submitted = 0, completed = 0, rejected = 0, batches = 0, sites_completed = 0;
+    int64_t submitted = 0, completed = 0, rejected = 0, batches = 0, sites_completed = 0, arena_misses = 0;
     std::vector<double> lat_ms;
+    std::vector<double> phase_ms[4];    // submit->admit, admit->ready, ready->launch, launch->done
     bool have_first = false;
     Clock::time_point t_first, t_last;
 
@@ -295,6 +297,9 @@ void retire(ccl_server *S, Batch &b) {
         S->completed++;
         S->sites_completed += r->n;
         S->lat_ms.push_back(std::chrono::duration<double, std::milli>(now - r->t_submit).count());
+        const Clock::time_point tp[5] = {r->t_submit, r->t_admit, r->t_ready, r->t_launch, now};
+        for (int k = 0; k < 4; ++k)
+            S->phase_ms[k].push_back(std::chrono::duration<double, std::milli>(tp[k + 1] - tp[k]).count());
         r->v_row_ptr.clear(); r->v_row_ptr.shrink_to_fit();
         r->v_col_idx.clear(); r->v_col_idx.shrink_to_fit();
         r->v_bits.clear(); r->v_bits.shrink_to_fit();
@@ -332,6 +337,8 @@ bool start_upload(ccl_server *S, const std::shared_ptr<Req> &r, cudaStream_t up)
 
 void launch_batch(ccl_server *S, int slot, std::vector<std::shared_ptr<Req>> reqs) {
     cudaStream_t s = S->streams[(size_t)slot];
+    const auto t_launch = Clock::now();
+    for (auto &r : reqs) r->t_launch = t_launch;
     std::vector<ccl::Inst> table;
     table.reserve(reqs.size());
     for (auto &r : reqs) {
@@ -396,17 +403,20 @@ void server_loop(ccl_server *S) {
     cudaSetDevice(S->cfg.device);
     for (;;) {
         bool progressed = false;
-        // 1. collect uploaded requests (admission and uploads run on the uploader thread)
+        // 1. collect every request whose upload has finished, in any order (a
+        //    large upload still in flight does not hold back the small ones
+        //    behind it; admission and uploads run on the uploader threads)
         {
             std::lock_guard<std::mutex> lk(S->mu);
             if (S->stop) break;
-            while (!S->uploading.empty()) {
-                auto &r = S->uploading.front();
+            for (auto it = S->uploading.begin(); it != S->uploading.end();) {
+                auto &r = *it;
                 const cudaError_t e = cudaEventQuery(r->uploaded);
-                if (e == cudaErrorNotReady) break;
+                if (e == cudaErrorNotReady) { ++it; continue; }
                 if (e != cudaSuccess) { (void)cudaGetLastError(); r->status = CCL_ERR_CUDA; }
+                r->t_ready = Clock::now();
                 S->ready.push_back(r);
-                S->uploading.pop_front();
+                it = S->uploading.erase(it);
                 progressed = true;
             }
         }
@@ -502,6 +512,7 @@ void upload_loop(ccl_server *S, cudaStream_t up) {
         S->pending.pop_front();
         S->held += r->dev_bytes + r->ws_bytes;
         S->held_req += r->dev_bytes;
+        r->t_admit = Clock::now();
         lk.unlock();
         const bool ok = start_upload(S, r, up);
         lk.lock();
@@ -664,11 +675,13 @@ ccl_status server_submit(ccl_server *S, const ccl_request *req, uint64_t *ticket
         std::lock_guard<std::mutex> lk(S->mu);
         r->lab_h = (int32_t *)S->arena.alloc((size_t)r->n * 4 + 4);
         if (r->lab_h) r->lab_bytes = (size_t)r->n * 4 + 4;
+        else S->arena_misses++;
     } else {
         {
             std::lock_guard<std::mutex> lk(S->mu);
             r->h = S->arena.alloc(lay.total);
             if (r->h) r->h_bytes = lay.total;
+            else S->arena_misses++;
         }
         if (r->h) {
             S->copier->copy(r->h, req->row_ptr, (size_t)(r->n + 1) * 4);
@@ -756,6 +769,14 @@ ccl_status ccl_server_stats_get(ccl_server *S, ccl_server_stats *out) {
     out->batches = S->batches;
     out->sites_completed = S->sites_completed;
     out->waiting = S->waiters;
+    out->arena_misses = S->arena_misses;
+    for (int k = 0; k < 4; ++k) {
+        if (S->phase_ms[k].empty()) continue;
+        std::vector<double> v = S->phase_ms[k];
+        std::sort(v.begin(), v.end());
+        out->phase_p50_ms[k] = v[std::min(v.size() - 1, (size_t)(0.5 * (double)(v.size() - 1) + 0.5))];
+        out->phase_p99_ms[k] = v[std::min(v.size() - 1, (size_t)(0.99 * (double)(v.size() - 1) + 0.5))];
+    }
     if (!S->lat_ms.empty()) {
         std::vector<double> v = S->lat_ms;
         std::sort(v.begin(), v.end());
