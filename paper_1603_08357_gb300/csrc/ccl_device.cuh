@@ -573,15 +573,19 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
                 if (has0) init_scan_chunk<kBatched, kGen>(P, S, I, cc0, lane, tc, c0);
                 if (has1) init_scan_chunk<kBatched, kGen>(P, S, I, cc1, lane, tc, c1);
             }
-            if (has0 && c0.i < I.n) I.labels[c0.i] = c0.lab;
-            if (has1 && c1.i < I.n) I.labels[c1.i] = c1.lab;
+            // the pair count's prefix sum and the band counter first: the
+            // shortcut label loads of the scan (c0.lab, c1.lab) land meanwhile
             const int rr = c0.r + c1.r;
             const int incl = warp_incl_scan(rr, lane);
             const int total = __shfl_sync(kFull, incl, 31);
+            unsigned long long base = 0;
             if (total > 0) {
-                unsigned long long base = 0;
                 if (lane == 0) base = atomicAdd(&band_cnt, (unsigned long long)total);
                 base = __shfl_sync(kFull, base, 0);
+            }
+            if (has0 && c0.i < I.n) I.labels[c0.i] = c0.lab;
+            if (has1 && c1.i < I.n) I.labels[c1.i] = c1.lab;
+            if (total > 0) {
                 if (lane == 0) my_pairs += (unsigned long long)total;
                 const int64_t slot = S.h.qband + (int64_t)base + (incl - rr);
                 if (c0.r > 0) init_emit_chunk<kBatched, kGen>(P, S, I, c0, slot);

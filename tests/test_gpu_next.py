@@ -274,3 +274,22 @@ def test_largest_cluster_crossing_near_exact_threshold(ctx):
     x, err = P.crossing(ps, curves[0][0], curves[1][0], se=(curves[0][1], curves[1][1]))
     assert x is not None and err is not None and err < 0.01
     assert abs(x - pc) < 0.012, (x, err)
+
+
+@pytest.mark.parametrize("kind,Ls,reps", [("triangle", 512, 12), ("honeycomb", 362, 12), ("triangle", 4096, 2)])
+def test_sweep_at_the_papers_sizes_matches_oracle(ctx, kind, Ls, reps):
+    """The device sweep at the sizes of Section 4 (N = 262,144 and 16,777,216
+    sites; honeycomb 362 x 362 cells = 262,088 sites): spanning flag and
+    largest cluster (size, label) of every realisation equal the oracle's on
+    the same keyed bonds."""
+    from paper_1603_08357_gb300 import percolation as P
+    lat = L.make_instance(dict(kind=kind, L=Ls, p=0.0, seed=0, periodic_y=False))
+    top, bot = P.boundary_rows(kind, Ls)
+    pc = P.PC_EXACT[kind]
+    ps = [pc - 0.003, pc, pc + 0.003]
+    span, big = P.Sampler(ctx, lat, top, bot).sweep(ps, reps, seed0=2024)
+    for a, p in enumerate(ps):
+        for r in range(reps):
+            lab = oracle.uf_label(dataclasses.replace(lat, open_bits=oracle.keyed_bits(lat, 2024 + r, p)))
+            assert tuple(big[a, r]) == stats.largest_cluster(lab), (kind, Ls, p, r)
+            assert bool(span[a, r]) == (stats.spanning_label(lab, top, bot) >= 0), (kind, Ls, p, r)
