@@ -520,24 +520,11 @@ def _settings(stats) -> dict:
                                                  "reduce_window", "analysis_group", "analysis_park")}
 
 
-def _pin(arrays):
-    """Page-locks host numpy arrays in place (cudaHostRegister through
-    torch's runtime binding) so that copies from and to them run at the
-    host link's full rate; returns an undo function."""
+def _pinned(a: np.ndarray) -> np.ndarray:
+    """A copy of a host array in a pinned host allocation (cudaHostAlloc
+    through torch), as a numpy array sharing that memory."""
     import torch
-    rt = torch.cuda.cudart()
-    done = []
-    for a in arrays:
-        if a.nbytes == 0:
-            continue
-        if int(rt.cudaHostRegister(a.ctypes.data, a.nbytes, 0)) != 0:
-            raise RuntimeError("cudaHostRegister failed")
-        done.append(a)
-
-    def undo():
-        for a in done:
-            rt.cudaHostUnregister(a.ctypes.data)
-    return undo
+    return torch.from_numpy(a.view(np.int32)).pin_memory().numpy().view(a.dtype)
 
 
 def run_batched(args, rank, world, local):
@@ -566,6 +553,13 @@ def run_batched(args, rank, world, local):
     b = L.make_batch(specs)
     abits, word_off = b.aligned_bits()
     t_gen = time.perf_counter() - t_gen
+    # the concatenated arrays move into pinned host allocations (the host side
+    # of the e2e leg, and what every other leg reads too)
+    t_pin = time.perf_counter()
+    import dataclasses
+    b = dataclasses.replace(b, row_ptr=_pinned(b.row_ptr), col_idx=_pinned(b.col_idx),
+                            open_bits=_pinned(b.open_bits))
+    t_pin = time.perf_counter() - t_pin
     rp = torch.from_numpy(b.row_ptr).to(dev)
     ci = torch.from_numpy(b.col_idx).to(dev)
     bits = torch.from_numpy(b.open_bits.view(np.int32)).to(dev)
@@ -662,8 +656,7 @@ def run_batched(args, rank, world, local):
     # buffers of its own for the host path)
     del rp, ci, bits
     torch.cuda.empty_cache()
-    h_lab = np.empty(b.n_total, np.int32)
-    unpin = _pin([b.row_ptr, b.col_idx, b.open_bits, h_lab])
+    h_lab = _pinned(np.empty(b.n_total, np.int32))
     h2d = b.row_ptr.nbytes + b.col_idx.nbytes + b.open_bits.nbytes
     d2h = h_lab.nbytes
 
@@ -684,7 +677,6 @@ def run_batched(args, rank, world, local):
         e2e_step()
         e_step_ms.append(1e3 * (time.perf_counter() - t1))
     e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / e_steps, dist, dev)
-    unpin()
     e2e_same = bool(np.array_equal(h_lab, got))
 
     if rank == 0:
@@ -717,7 +709,8 @@ def run_batched(args, rank, world, local):
             "config": {"workload": "batched", "instances": b.k, "n_sites": b.n_total, "nnz": b.nnz_total,
                        "desc": "4096 mixed honeycomb / triangle / Cayley-tree instances at p_c +- 0.05, "
                                "concatenated CSR with int64 offsets",
-                       "residual_pairs": q, "generation_s": t_gen, "options": opts, "autotune": tuned,
+                       "residual_pairs": q, "generation_s": t_gen, "pinning_s": t_pin, "options": opts,
+                       "autotune": tuned,
                        "l2": "inputs larger than L2 (no flush)",
                        "parallelism": f"replicas{world}" if world > 1 else "single"},
             "one_at_a_time": {"value": world * b.n_total / (ms_one / 1e3), "unit": "sites/s",
@@ -735,7 +728,7 @@ def run_batched(args, rank, world, local):
             "e2e": {"value": world * b.n_total / (e_ms / 1e3), "unit": "sites/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e_ms,
                     "step_ms": [round(x, 2) for x in e_step_ms],
-                    "entry": "ccl_label_batched_host (page-locked host arrays)",
+                    "entry": "ccl_label_batched_host (pinned host allocations)",
                     "labels_identical": e2e_same},
             "gpu_launches": args.steps * (4 if opts["pre_analysis"] else 3),
             "clocks": clk,
@@ -756,8 +749,9 @@ def run_served(args, rank, world, local):
     loop, both submission modes), then Poisson arrivals at fractions of that
     capacity (open loop) for the latency percentiles. The stream repeats a
     pool of distinct pre-generated requests (the whole stream would not fit in
-    host memory); the pool's arrays are page-locked once, as a serving
-    process keeps its request buffers."""
+    host memory); the pool's arrays and the result buffers live in pinned
+    host allocations, as a serving process keeps its request buffers."""
+    import dataclasses
     import torch
     torch.cuda.set_device(local)
     import paper_1603_08357_gb300 as ccl
@@ -765,11 +759,12 @@ def run_served(args, rank, world, local):
     specs = L.served_specs(args.requests, seed=5 + 1000 * rank)
     pool = [L.make_instance(sp) for sp in specs[:args.pool]]
     t_gen = time.perf_counter() - t_gen
+    pool = [dataclasses.replace(lat, row_ptr=_pinned(lat.row_ptr), col_idx=_pinned(lat.col_idx),
+                                open_bits=_pinned(lat.open_bits)) for lat in pool]
     req = [pool[r % len(pool)] for r in range(args.requests)]
     total_sites = sum(lat.n for lat in req)
     mean_sites = total_sites / len(req)
-    out_bufs = {id(lat): np.empty(lat.n, np.int32) for lat in pool}
-    unpin = _pin([a for lat in pool for a in (lat.row_ptr, lat.col_idx, lat.open_bits)] + list(out_bufs.values()))
+    out_bufs = {id(lat): _pinned(np.empty(lat.n, np.int32)) for lat in pool}
     keep_idx = set(range(0, len(req), max(1, len(req) // args.parity_sample)))
 
     def submit_with(fn, name):
@@ -898,7 +893,6 @@ def run_served(args, rank, world, local):
                             "p50_ms": so.p50_ms, "p99_ms": so.p99_ms, "max_ms": so.max_ms,
                             "batches": int(so.batches), "arena_misses": int(so.arena_misses),
                             "phases": _phases(so)}
-    unpin()
 
     ok = None
     if rank == 0:
@@ -926,7 +920,7 @@ def run_served(args, rank, world, local):
             "config": {"workload": "served", "requests": len(req), "pool": len(pool),
                        "mean_sites": mean_sites, "window": args.window, "streams": args.streams,
                        "client_waiters": args.waiters,
-                       "generation_s": t_gen, "host_arrays": "page-locked",
+                       "generation_s": t_gen, "host_arrays": "pinned allocations (cudaHostAlloc)",
                        "l2": "inputs larger than L2 in aggregate (no flush)"},
             "closed_loop": {"submit": "ccl_server_submit_nocopy", "wall_s": wall,
                             "requests_per_s": len(req) / wall, "batches": int(st_closed.batches),
