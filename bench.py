@@ -535,7 +535,7 @@ def run_batched(args, rank, world, local):
     value: batched sites/s from per-step CUDA events, inputs resident in HBM.
     roofline: the dominant kernel of the batched step (per-kernel events of
     the same timed steps) against the measured copy bandwidth.
-    e2e: ccl_label_batched_host from page-locked host arrays (inputs up,
+    e2e: ccl_label_batched_host from pinned host allocations (inputs up,
     labels down, inside the timed region).
     cpu_baseline: the union-find oracle over every instance of the batch,
     whole instances spread over the host's cores; it also checks every label
@@ -651,7 +651,7 @@ def run_batched(args, rank, world, local):
     del out1, ab0
     ccl.ccl_context_destroy(one)
 
-    # end to end from page-locked host arrays through ccl_label_batched_host;
+    # end to end from pinned host allocations through ccl_label_batched_host;
     # the device copies of the inputs are dropped first (the context keeps
     # buffers of its own for the host path)
     del rp, ci, bits
