@@ -464,13 +464,33 @@ __device__ __forceinline__ bool init_scan_pair(const Params &P, const Stage &S, 
     if (jmax >= (uint32_t)n) raise_err(P.err, kErrIndex);
     const int n0 = __popc(l0), n1 = __popc(l1);
     int32_t lab0 = n0 ? m0 : i0, lab1 = n1 ? m1 : i1;
-    if (n0) {
-        const int32_t mt = (int32_t)((uint32_t)m0 / kTileSites);
-        if (mt >= tc.vis_lo && mt <= tc.vis_hi) lab0 = __ldcg(I.labels + m0);
+    // Pointer jumping inside the warp's window of 64 sites [s00, s00 + 64): a
+    // label that points to a window site takes that site's label, until it
+    // leaves the window or reaches a site that is its own label. Every value
+    // taken is an ancestor of the site, so it stays a valid label, and chains
+    // along a lattice row collapse to one hop per window.
+    // (A chunk-0 label lies below its site, so inside the window it points
+    // into chunk 0; a chunk-1 label may point into either chunk.)
+    bool jump = __any_sync(kFull, (uint32_t)(lab0 - s00) < 64u || (uint32_t)(lab1 - s00) < 64u);
+    for (int it = 0; jump && it < 6; ++it) {
+        const uint32_t w0 = (uint32_t)(lab0 - s00), w1 = (uint32_t)(lab1 - s00);
+        const int32_t a0v = __shfl_sync(kFull, lab0, (int)(w0 & 31u));
+        const int32_t a1v = __shfl_sync(kFull, lab0, (int)(w1 & 31u)), b1v = __shfl_sync(kFull, lab1, (int)(w1 & 31u));
+        const int32_t n0v = w0 < 32u ? a0v : lab0;
+        const int32_t n1v = w1 < 64u ? (w1 < 32u ? a1v : b1v) : lab1;
+        jump = __any_sync(kFull, n0v != lab0 || n1v != lab1);
+        lab0 = n0v;
+        lab1 = n1v;
     }
-    if (n1) {
-        const int32_t mt = (int32_t)((uint32_t)m1 / kTileSites);
-        if (mt >= tc.vis_lo && mt <= tc.vis_hi) lab1 = __ldcg(I.labels + m1);
+    // a label before the window in a tile of this band finished kStages tiles
+    // ago: take that site's label (the band shortcut)
+    if (lab0 < s00) {
+        const int32_t mt = (int32_t)((uint32_t)lab0 / kTileSites);
+        if (mt >= tc.vis_lo && mt <= tc.vis_hi) lab0 = __ldcg(I.labels + lab0);
+    }
+    if (lab1 < s00) {
+        const int32_t mt = (int32_t)((uint32_t)lab1 / kTileSites);
+        if (mt >= tc.vis_lo && mt <= tc.vis_hi) lab1 = __ldcg(I.labels + lab1);
     }
     c0.i = i0; c0.a = a0; c0.a_next = b0; c0.mk = k0; c0.lab = lab0; c0.fast = true;
     c0.resmask = n0 ? (l0 & ~(1u << k0)) : 0u; c0.r = n0 > 1 ? n0 - 1 : 0;
