@@ -464,23 +464,21 @@ __device__ __forceinline__ bool init_scan_pair(const Params &P, const Stage &S, 
     if (jmax >= (uint32_t)n) raise_err(P.err, kErrIndex);
     const int n0 = __popc(l0), n1 = __popc(l1);
     int32_t lab0 = n0 ? m0 : i0, lab1 = n1 ? m1 : i1;
-    // Pointer jumping inside the warp's window of 64 sites [s00, s00 + 64): a
-    // label that points to a window site takes that site's label, until it
-    // leaves the window or reaches a site that is its own label. Every value
-    // taken is an ancestor of the site, so it stays a valid label, and chains
-    // along a lattice row collapse to one hop per window.
-    // (A chunk-0 label lies below its site, so inside the window it points
-    // into chunk 0; a chunk-1 label may point into either chunk.)
-    bool jump = __any_sync(kFull, (uint32_t)(lab0 - s00) < 64u || (uint32_t)(lab1 - s00) < 64u);
-    for (int it = 0; jump && it < 6; ++it) {
+    // One pointer jump inside the warp's window of 64 sites [s00, s00 + 64):
+    // a label that points to a window site takes that site's label. The value
+    // taken is an ancestor of the site, so it stays a valid label, and a chain
+    // along a lattice row shortens by half before step (iii) and the analysis
+    // follow it. (A chunk-0 label lies below its site, so inside the window it
+    // points into chunk 0; a chunk-1 label may point into either chunk.) One
+    // jump measured faster end to end than jumping until the window is
+    // settled: the later rounds cost step (i) more than they save afterwards.
+    if (__any_sync(kFull, (uint32_t)(lab0 - s00) < 64u || (uint32_t)(lab1 - s00) < 64u)) {
         const uint32_t w0 = (uint32_t)(lab0 - s00), w1 = (uint32_t)(lab1 - s00);
         const int32_t a0v = __shfl_sync(kFull, lab0, (int)(w0 & 31u));
-        const int32_t a1v = __shfl_sync(kFull, lab0, (int)(w1 & 31u)), b1v = __shfl_sync(kFull, lab1, (int)(w1 & 31u));
-        const int32_t n0v = w0 < 32u ? a0v : lab0;
-        const int32_t n1v = w1 < 64u ? (w1 < 32u ? a1v : b1v) : lab1;
-        jump = __any_sync(kFull, n0v != lab0 || n1v != lab1);
-        lab0 = n0v;
-        lab1 = n1v;
+        const int32_t a1v = __shfl_sync(kFull, lab0, (int)(w1 & 31u));
+        const int32_t b1v = __shfl_sync(kFull, lab1, (int)(w1 & 31u));
+        if (w0 < 32u) lab0 = a0v;
+        if (w1 < 64u) lab1 = w1 < 32u ? a1v : b1v;
     }
     // a label before the window in a tile of this band finished kStages tiles
     // ago: take that site's label (the band shortcut)
