@@ -530,6 +530,35 @@ __device__ __forceinline__ void init_emit_chunk(const Params &P, const Stage &S,
     }
 }
 
+// Both chunks of a warp on the register path: the residual pairs of a lane's
+// two sites in one loop (chunk 0's bits low, chunk 1's from bit 16), with a
+// warp-uniform trip count, so the warp neither diverges nor loops twice.
+// The queue order is that of init_emit_chunk on chunk 0 then chunk 1.
+template <bool kBatched>
+__device__ __forceinline__ void init_emit_pair(const Params &P, const Stage &S, const ChunkRes &c0,
+                                               const ChunkRes &c1, int64_t slot, int rr) {
+    const StageHdr &h = S.h;
+    const int iters = (int)__reduce_max_sync(kFull, (uint32_t)rr);
+    uint32_t mm = c0.resmask | (c1.resmask << 16);
+    if (slot + rr > P.q_cap) {                  // corrupt rows only
+        if (rr > 0) raise_err(P.err, kErrIndex);
+        mm = 0;
+    }
+    const int32_t offA = c0.a - h.ci_lo, offB = c1.a - h.ci_lo - 16;
+    int2 *qp = P.q + slot;
+    int32_t *kp = kBatched ? P.qk + slot : nullptr;
+    for (int it = 0; it < iters; ++it) {
+        if (mm) {
+            const int t = __ffs(mm) - 1;
+            mm &= mm - 1;
+            const bool hi = t >= 16;
+            const int32_t j = S.ci[(hi ? offB : offA) + t];
+            *qp++ = make_int2(hi ? c1.lab : c0.lab, j);
+            if (kBatched) *kp++ = h.k;
+        }
+    }
+}
+
 template <bool kBatched, bool kGen = false>
 __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -586,6 +615,8 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
             const int cc0 = warp * 2, cc1 = warp * 2 + 1;
             ChunkRes c0, c1;
             c0.r = c1.r = 0;
+            c0.resmask = c1.resmask = 0u;
+            c0.fast = c1.fast = true;
             const bool has0 = cc0 * kChunk < S.h.ts, has1 = cc1 * kChunk < S.h.ts;
             if (!(has1 && init_scan_pair<kBatched, kGen>(P, S, I, cc0, lane, tc, c0, c1))) {
                 if (has0) init_scan_chunk<kBatched, kGen>(P, S, I, cc0, lane, tc, c0);
@@ -606,8 +637,12 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
             if (total > 0) {
                 if (lane == 0) my_pairs += (unsigned long long)total;
                 const int64_t slot = S.h.qband + (int64_t)base + (incl - rr);
-                if (c0.r > 0) init_emit_chunk<kBatched, kGen>(P, S, I, c0, slot);
-                if (c1.r > 0) init_emit_chunk<kBatched, kGen>(P, S, I, c1, slot + c0.r);
+                if (c0.fast && c1.fast) {
+                    init_emit_pair<kBatched>(P, S, c0, c1, slot, rr);
+                } else {
+                    if (c0.r > 0) init_emit_chunk<kBatched, kGen>(P, S, I, c0, slot);
+                    if (c1.r > 0) init_emit_chunk<kBatched, kGen>(P, S, I, c1, slot + c0.r);
+                }
             }
         }
         __syncwarp();
