@@ -859,6 +859,28 @@ __global__ void __launch_bounds__(256) k_analysis_park(Params P) {
 
 enum : int32_t { kTaskDone = 0, kTaskChase = 1, kTaskRoot = 2, kTaskMerge = 3 };
 
+// Next state of a slot, 2 bits at index 4 * state + 2 * (y == a) + (y == b):
+//   Done  -> Done;
+//   Chase -> y == a: Root (link mode 0) or Merge (link mode 1);
+//            else y == b: Done (one tree); else Chase;
+//   Root  -> y == b: Merge; else Root;
+//   Merge -> y == a or y == b: Done; else Merge.
+constexpr uint32_t red_next_table(int link_mode) {
+    uint32_t t = 0;
+    for (uint32_t idx = 0; idx < 16; ++idx) {
+        const uint32_t s = idx >> 2;
+        const bool eq_a = (idx & 2u) != 0, eq_b = (idx & 1u) != 0;
+        uint32_t nx = kTaskDone;
+        if (s == kTaskChase) nx = eq_a ? (link_mode ? kTaskMerge : kTaskRoot) : (eq_b ? kTaskDone : kTaskChase);
+        else if (s == kTaskRoot) nx = eq_b ? kTaskMerge : kTaskRoot;
+        else if (s == kTaskMerge) nx = (eq_a || eq_b) ? kTaskDone : kTaskMerge;
+        t |= nx << (2u * idx);
+    }
+    return t;
+}
+constexpr uint32_t kRedNextLink0 = red_next_table(0), kRedNextLink1 = red_next_table(1);
+
+
 // Chase loads may be served from L1: a stale label is an older ancestor,
 // which only lengthens a walk (labels only decrease), and every merge goes
 // through an atomicMin whose returned value is current.
@@ -1005,7 +1027,16 @@ __global__ void __launch_bounds__(256) k_reduce(Params P) {
                 if (st[u] == kTaskMerge) v[u] = atomicMin(ptr, b[u]);
                 else if (st[u] != kTaskDone) v[u] = red_load(ptr);
             }
-            // use: the next state of every slot by selects (no divergent paths)
+            // use: the next state of every slot (no divergent paths). With
+            // mx = max(y, b) and mn = min(y, b) every transition sets b = mn
+            // and a = mx, except Root, which keeps a:
+            //   Chase (y = label[a]): y == a means a root, so mx = a, mn = b;
+            //     otherwise the walk goes on from the larger node;
+            //   Root (y = label[b] <= b): b = y;
+            //   Merge (y = old label[a]): Algorithm 1 continues with (old, b)
+            //     when old > b and with (b, old) when old < b.
+            // The next state is looked up by (state, y == a, y == b).
+            const uint32_t table = P.link_mode ? kRedNextLink1 : kRedNextLink0;
             bool any = false;
 #pragma unroll
             for (int u = 0; u < kRedSlots; ++u) {
@@ -1015,19 +1046,10 @@ __global__ void __launch_bounds__(256) k_reduce(Params P) {
                 st_hops += (s == kTaskChase || s == kTaskRoot);
                 st_atom += (s == kTaskMerge);
 #endif
-                const bool c_root = y == A, c_hit = y == Bv;
-                const int32_t ca = c_root ? A : max(y, Bv), cb = c_root ? Bv : min(y, Bv);
-                const int cs = c_root ? (P.link_mode ? kTaskMerge : kTaskRoot) : (c_hit ? kTaskDone : kTaskChase);
-                const bool r_root = y == Bv;
-                const int32_t rb = r_root ? Bv : y;
-                const int rs = r_root ? kTaskMerge : kTaskRoot;
-                const bool m_done = (y == Bv) || (y == A);
-                const bool m_gt = y > Bv;
-                const int32_t ma = m_gt ? y : Bv, mb = m_gt ? Bv : y;
-                const int ms = m_done ? kTaskDone : kTaskMerge;
-                a[u] = s == kTaskChase ? ca : (s == kTaskMerge ? ma : A);
-                b[u] = s == kTaskChase ? cb : (s == kTaskRoot ? rb : (s == kTaskMerge ? mb : Bv));
-                st[u] = s == kTaskChase ? cs : (s == kTaskRoot ? rs : (s == kTaskMerge ? ms : s));
+                const uint32_t idx = ((uint32_t)s << 2) | ((y == A) ? 2u : 0u) | ((y == Bv) ? 1u : 0u);
+                a[u] = s == kTaskRoot ? A : max(y, Bv);
+                b[u] = min(y, Bv);
+                st[u] = (int32_t)((table >> (2u * idx)) & 3u);
                 any |= st[u] != kTaskDone;
             }
             if (!__any_sync(kFull, any || pf_ok) && (kStatic || nxt >= wlen)) break;
