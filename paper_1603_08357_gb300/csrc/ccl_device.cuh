@@ -14,8 +14,8 @@
 //    smallest lower neighbour lies in a band tile finished kStages tiles
 //    earlier takes that neighbour's label (most of step (ii) on lattices).
 //  * Step (iii) runs Algorithm 1 over the queue: each warp drains a window of
-//    pairs with four pairs per lane in lockstep rounds (one load or atomicMin
-//    per live pair per round, next state by selects).
+//    pairs with kRedSlots (six) pairs per lane in lockstep rounds (one load
+//    or atomicMin per live pair per round, next state from a small table).
 //  * Steps (ii)/(iv) chase every site's chain to its root, two chains per
 //    lane at once, each warp over a contiguous range of sites (or
 //    interleaved, for inputs without locality).

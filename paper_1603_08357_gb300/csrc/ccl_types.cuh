@@ -32,7 +32,7 @@ constexpr int kAnaChunks = CCL_ANA_CHUNKS;
 // step (iii): pairs a lane carries at once; pairs a warp drains per window;
 // most step-(i) CTAs (bands)
 #ifndef CCL_RED_SLOTS
-#define CCL_RED_SLOTS 4
+#define CCL_RED_SLOTS 6
 #endif
 constexpr int kRedSlots = CCL_RED_SLOTS;
 constexpr int kRedWindowMax = 2048;   // default most pairs per warp window (fewer for small queues)
