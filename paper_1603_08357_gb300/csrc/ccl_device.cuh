@@ -682,8 +682,11 @@ __global__ void __launch_bounds__(512) k_analysis(Params P) {
     // or runs of ana_group groups every nwarps * ana_group groups
     const int64_t G = !kSeq ? 1 : (P.ana_group > 0 && P.ana_group < per ? (int64_t)P.ana_group : per);
     const int64_t sc_stride = kSeq ? nwarps * G : nwarps;
-    int kc = 0;                          // cached instance and its chunk range
+    // the instance of the current chunks, its chunk range and the fields used,
+    // kept in registers until a chunk of another instance comes
     int64_t kc_lo = 0, kc_hi = kBatched ? 0 : P.n_chunks;
+    int32_t *kc_lab = P.one.labels;
+    int32_t kc_n = P.one.n;
     for (int64_t run = wid * G; run < ngroups; run += sc_stride)
     for (int64_t gidx = run; gidx < min(run + G, ngroups); ++gidx) {
         int32_t *L[kAnaChunks];
@@ -698,15 +701,16 @@ __global__ void __launch_bounds__(512) k_analysis(Params P) {
             site[u] = 0;
             if (c < P.n_chunks) {
                 if (kBatched && (c < kc_lo || c >= kc_hi)) {
-                    kc = find_inst(P, c);
+                    const int kc = find_inst(P, c);
                     kc_lo = P.insts[kc].chunk_begin;
                     kc_hi = kc + 1 < P.K ? P.insts[kc + 1].chunk_begin : P.n_chunks;
+                    kc_lab = P.insts[kc].labels;
+                    kc_n = P.insts[kc].n;
                 }
-                const Inst I = inst_of<kBatched>(P, kc);
-                site[u] = (int32_t)((c - I.chunk_begin) * kChunk) + lane;
-                L[u] = I.labels;
-                cap = max(cap, I.n);
-                act[u] = site[u] < I.n;
+                site[u] = (int32_t)((c - (kBatched ? kc_lo : P.one.chunk_begin)) * kChunk) + lane;
+                L[u] = kc_lab;
+                cap = max(cap, kc_n);
+                act[u] = site[u] < kc_n;
             }
         }
         // all loads of a round are issued before any result is used, so the
@@ -956,6 +960,10 @@ __global__ void __launch_bounds__(256) k_reduce(Params P) {
         int2 pf = make_int2(0, 0);
         int pfk = 0;
         bool pf_ok = false;
+        // batched: the labels of the lane's last instance (consecutive pairs
+        // of a lane mostly come from one instance)
+        int lk = 0;
+        int32_t *llab = kBatched ? P.insts[0].labels : P.one.labels;
         auto fetch = [&](long long p) {
             while (s_pref[cur + 1] <= p) ++cur;
             const long long slot = P.band[cur].qbase + (p - s_pref[cur]);
@@ -981,7 +989,8 @@ __global__ void __launch_bounds__(256) k_reduce(Params P) {
                     if (st[u] == kTaskDone) take = u;
                 if (take >= 0 && pf_ok) {
                     const int32_t na = max(pf.x, pf.y), nb = min(pf.x, pf.y);
-                    int32_t *nl = kBatched ? P.insts[pfk].labels : P.one.labels;
+                    if (kBatched && pfk != lk) { lk = pfk; llab = P.insts[pfk].labels; }
+                    int32_t *nl = llab;
 #pragma unroll
                     for (int u = 0; u < kRedSlots; ++u)
                         if (u == take) { a[u] = na; b[u] = nb; st[u] = kTaskChase; L[u] = nl; }
@@ -1003,7 +1012,11 @@ __global__ void __launch_bounds__(256) k_reduce(Params P) {
                             while (s_pref[bb + 1] <= p) ++bb;
                             const long long slot = P.band[bb].qbase + (p - s_pref[bb]);
                             const int2 pr = P.q[slot];
-                            if (kBatched) L[u] = P.insts[P.qk[slot]].labels;
+                            if (kBatched) {
+                                const int k = P.qk[slot];
+                                if (k != lk) { lk = k; llab = P.insts[k].labels; }
+                                L[u] = llab;
+                            }
                             a[u] = max(pr.x, pr.y);
                             b[u] = min(pr.x, pr.y);
                             st[u] = kTaskChase;
