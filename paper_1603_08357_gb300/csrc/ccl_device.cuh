@@ -964,9 +964,14 @@ __global__ void __launch_bounds__(256) k_reduce(Params P) {
         // of a lane mostly come from one instance)
         int lk = 0;
         int32_t *llab = kBatched ? P.insts[0].labels : P.one.labels;
+        // queue slot of pair p = qoff + p inside band `cur`
+        long long qoff = P.band[cur].qbase - s_pref[cur];
         auto fetch = [&](long long p) {
-            while (s_pref[cur + 1] <= p) ++cur;
-            const long long slot = P.band[cur].qbase + (p - s_pref[cur]);
+            if (s_pref[cur + 1] <= p) {
+                do { ++cur; } while (s_pref[cur + 1] <= p);
+                qoff = P.band[cur].qbase - s_pref[cur];
+            }
+            const long long slot = qoff + p;
             pf = P.q[slot];
             if (kBatched) pfk = P.qk[slot];
             pf_ok = true;
