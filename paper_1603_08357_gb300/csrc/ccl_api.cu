@@ -153,7 +153,7 @@ int blocks_per_sm(ccl_context *ctx, int kernel_id, int threads) {
         case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init<false>, kInitThreads, kInitSmem); break;
         case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init<true>, kInitThreads, kInitSmem); break;
         case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_analysis<false, true>, threads, 0); break;
-        case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_analysis<true, true>, threads, 0); break;
+        case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_analysis<true, true, kAnaChunksBatched>, threads, 0); break;
         case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_reduce<false, true>, threads, 0); break;
         case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_reduce<true, true>, threads, 0); break;
         case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_init<false, true>, kInitThreads, kInitSmem); break;
@@ -393,6 +393,7 @@ ccl_status enqueue_tail(ccl_context *ctx, const Params &P0, bool batched, const 
     note_settings(ctx, tc, P);
     const int T = tc.threads;
     const int64_t warps_chunks = (P.n_chunks + kAnaChunks - 1) / kAnaChunks;
+    const int64_t warps_chunks_b = (P.n_chunks + kAnaChunksBatched - 1) / kAnaChunksBatched;
     const int64_t g_red = (int64_t)ctx->num_sms * blocks_per_sm(ctx, batched ? 5 : 4, 256);
     if (profile) CCL_CUDA(cudaEventRecord(ctx->ev[1], s));
     const bool park = resolve_park(ctx, tc, P);
@@ -408,10 +409,10 @@ ccl_status enqueue_tail(ccl_context *ctx, const Params &P0, bool batched, const 
             else k_analysis_park<false><<<gp, 32 * kParkWarps, 0, s>>>(P);
             return;
         }
-        const unsigned g = (unsigned)grid_for(ctx, batched ? 3 : 2, tc, warps_chunks);
+        const unsigned g = (unsigned)grid_for(ctx, batched ? 3 : 2, tc, batched ? warps_chunks_b : warps_chunks);
         if (batched) {
-            if (tc.ana_seq) k_analysis<true, true><<<g, T, 0, s>>>(P);
-            else k_analysis<true, false><<<g, T, 0, s>>>(P);
+            if (tc.ana_seq) k_analysis<true, true, kAnaChunksBatched><<<g, T, 0, s>>>(P);
+            else k_analysis<true, false, kAnaChunksBatched><<<g, T, 0, s>>>(P);
         } else {
             if (tc.ana_seq) k_analysis<false, true><<<g, T, 0, s>>>(P);
             else k_analysis<false, false><<<g, T, 0, s>>>(P);

@@ -658,8 +658,9 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
 // Steps (ii) and (iv): analysis. Every site follows its label chain to the
 // root and stores the root. No atomics run concurrently with this kernel and
 // every value written is an ancestor of the site, so plain stores are safe.
-// A warp walks kAnaChunks chunks at once (one chain per lane per chunk) so
-// that their dependent loads overlap.
+// A warp walks kCh chunks at once (one chain per lane per chunk) so that
+// their dependent loads overlap: kAnaChunks for one instance, more for a
+// batch, whose labels do not fit L2 (longer latencies to cover).
 
 // kSeq = true: warp w walks contiguous runs of chunk groups in increasing
 // order, so the chains of its later sites run into roots it has already
@@ -671,11 +672,11 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
 // same instances) stay within L2 when the whole array does not fit.
 // kSeq = false: groups are interleaved over the warps (grid stride), which
 // balances inputs without locality (randomly numbered trees).
-template <bool kBatched, bool kSeq>
+template <bool kBatched, bool kSeq, int kCh = kAnaChunks>
 __global__ void __launch_bounds__(512) k_analysis(Params P) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t ngroups = (P.n_chunks + kAnaChunks - 1) / kAnaChunks;
+    const int64_t ngroups = (P.n_chunks + kCh - 1) / kCh;
     const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int64_t per = (ngroups + nwarps - 1) / nwarps;
     // run length G and super-chunk stride: one run of `per` groups per warp,
@@ -689,13 +690,13 @@ __global__ void __launch_bounds__(512) k_analysis(Params P) {
     int32_t kc_n = P.one.n;
     for (int64_t run = wid * G; run < ngroups; run += sc_stride)
     for (int64_t gidx = run; gidx < min(run + G, ngroups); ++gidx) {
-        int32_t *L[kAnaChunks];
-        int32_t site[kAnaChunks], x[kAnaChunks], first[kAnaChunks];
+        int32_t *L[kCh];
+        int32_t site[kCh], x[kCh], first[kCh];
         int32_t cap = 0;
-        bool act[kAnaChunks];
+        bool act[kCh];
 #pragma unroll
-        for (int u = 0; u < kAnaChunks; ++u) {
-            const int64_t c = gidx * kAnaChunks + u;
+        for (int u = 0; u < kCh; ++u) {
+            const int64_t c = gidx * kCh + u;
             act[u] = false;
             L[u] = nullptr;
             site[u] = 0;
@@ -714,21 +715,21 @@ __global__ void __launch_bounds__(512) k_analysis(Params P) {
             }
         }
         // all loads of a round are issued before any result is used, so the
-        // kAnaChunks chains of a lane are in flight together
+        // kCh chains of a lane are in flight together
 #pragma unroll
-        for (int u = 0; u < kAnaChunks; ++u) x[u] = act[u] ? L[u][site[u]] : 0;
+        for (int u = 0; u < kCh; ++u) x[u] = act[u] ? L[u][site[u]] : 0;
 #pragma unroll
-        for (int u = 0; u < kAnaChunks; ++u) {
+        for (int u = 0; u < kCh; ++u) {
             first[u] = x[u];
             act[u] = act[u] && x[u] != site[u];
         }
         for (int32_t it = 0;; ++it) {
-            int32_t y[kAnaChunks];
+            int32_t y[kCh];
 #pragma unroll
-            for (int u = 0; u < kAnaChunks; ++u) y[u] = act[u] ? L[u][x[u]] : 0;
+            for (int u = 0; u < kCh; ++u) y[u] = act[u] ? L[u][x[u]] : 0;
             bool any = false;
 #pragma unroll
-            for (int u = 0; u < kAnaChunks; ++u) {
+            for (int u = 0; u < kCh; ++u) {
                 if (act[u]) {
                     if (y[u] == x[u]) act[u] = false;
                     else { x[u] = y[u]; any = true; }
@@ -738,7 +739,7 @@ __global__ void __launch_bounds__(512) k_analysis(Params P) {
             if (it > cap || (P.iter_cap > 0 && it + 1 >= P.iter_cap)) { raise_err(P.err, kErrNonconv); break; }
         }
 #pragma unroll
-        for (int u = 0; u < kAnaChunks; ++u)
+        for (int u = 0; u < kCh; ++u)
             if (L[u] && x[u] != first[u] && site[u] < cap) L[u][site[u]] = x[u];
     }
 }

@@ -28,6 +28,10 @@ constexpr int kRowRegs = 8;                // rows up to this degree are scanned
 #define CCL_ANA_CHUNKS 2
 #endif
 constexpr int kAnaChunks = CCL_ANA_CHUNKS;
+#ifndef CCL_ANA_CHUNKS_BATCHED
+#define CCL_ANA_CHUNKS_BATCHED 4
+#endif
+constexpr int kAnaChunksBatched = CCL_ANA_CHUNKS_BATCHED;
 
 // step (iii): pairs a lane carries at once; pairs a warp drains per window;
 // most step-(i) CTAs (bands)
