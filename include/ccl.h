@@ -224,13 +224,16 @@ CCL_API ccl_status ccl_label_host(ccl_context *ctx, int32_t n_sites, int64_t nnz
  * ccl_label_batched_host -- ccl_label_batched on HOST arrays (the same
  * layout, offsets and meaning): copies the concatenated inputs to context
  * buffers, labels, copies the labels back to `labels` (HOST
- * int32[site_off[K]]) and waits. Synchronous. The bit words go up first, then
- * the row pointers and columns in four groups of instances of about equal
- * site counts; step (i) on a group starts as soon as the group has arrived,
- * while the later groups are still being copied. The context keeps device
- * buffers of the inputs' size (plus the labels) for later calls. Pinned
- * host memory gives the full copy bandwidth. Errors: as ccl_label_batched,
- * plus the device status of ccl_sync.
+ * int32[site_off[K]]) and waits. Synchronous. The instances are labelled in
+ * eight groups of about equal site counts, each through all four steps: the
+ * upload of later groups and the download of the labels of earlier ones run
+ * on two streams of their own while a group is labelled, so the two
+ * directions of the host link are busy at once. The result is the same as
+ * one ccl_label_batched call; ccl_get_stats afterwards reports the whole
+ * batch (pair counts summed over the groups, the settings of the last
+ * group). The context keeps device buffers of the inputs' size (plus the
+ * labels) for later calls. Pinned host memory gives the full copy bandwidth.
+ * Errors: as ccl_label_batched, plus the device status of ccl_sync.
  */
 CCL_API ccl_status ccl_label_batched_host(ccl_context *ctx, int32_t n_inst, const int64_t *site_off,
                                           const int64_t *ent_off, const int32_t *row_ptr,

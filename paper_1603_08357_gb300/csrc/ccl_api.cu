@@ -84,6 +84,10 @@ struct ccl_context {
     int64_t host_in_cap = 0;
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t part_ev[5] = {};
+    // batched host-buffer path: the label download stream and, per instance
+    // group, the events of its upload and of its labelling
+    cudaStream_t d2h_stream = nullptr;
+    cudaEvent_t bh_up[8] = {}, bh_done[9] = {};
     // relabel / spanning scratch
     void *d_aux = nullptr;
     int64_t aux_cap = 0;
@@ -882,6 +886,9 @@ void ccl_context_destroy(ccl_context *ctx) {
     if (ctx->d_aux) cudaFree(ctx->d_aux);
     for (auto &e : ctx->part_ev) if (e) cudaEventDestroy(e);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    for (auto &e : ctx->bh_up) if (e) cudaEventDestroy(e);
+    for (auto &e : ctx->bh_done) if (e) cudaEventDestroy(e);
+    if (ctx->d2h_stream) cudaStreamDestroy(ctx->d2h_stream);
     if (ctx->staging_free) cudaEventDestroy(ctx->staging_free);
     if (ctx->stats_ev) cudaEventDestroy(ctx->stats_ev);
     for (auto &set : ctx->prof)
@@ -1413,73 +1420,107 @@ ccl_status ccl_label_batched_host(ccl_context *ctx, int32_t K, const int64_t *si
     ctx->last.n_sites = n_tot;
     ctx->last.nnz = nnz_tot;
     if (chunks == 0) return CCL_OK;
-    const bool batched = K > 1;
-    st = ensure_workspace(ctx, nnz_tot, batched);
+    st = ensure_workspace(ctx, nnz_tot, K > 1);
     if (st != CCL_OK) return st;
     if (!ctx->copy_stream) {
         CCL_CUDA(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
         for (auto &e : ctx->part_ev) CCL_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
-    const TuneChoice tc = choice_for_class(ctx, batch_class(n_tot, nnz_tot, K));
-    Params P = base_params(ctx, tc);
-    P.K = K;
-    P.n_chunks = chunks;
-    if (batched) {
-        st = upload_table(ctx, table, s);
-        if (st != CCL_OK) return st;
-        P.insts = ctx->d_insts;
-    } else {
-        P.one = table[0];
+    if (!ctx->d2h_stream) {
+        CCL_CUDA(cudaStreamCreateWithFlags(&ctx->d2h_stream, cudaStreamNonBlocking));
+        for (auto &e : ctx->bh_up) CCL_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        for (auto &e : ctx->bh_done) CCL_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
-    CCL_CUDA(cudaMemsetAsync(P.counters, 0, 4 * sizeof(unsigned long long), s));
-    CCL_CUDA(cudaMemsetAsync(P.band, 0, (size_t)kMaxBands * sizeof(BandRec), s));
+    const TuneChoice tc = choice_for_class(ctx, batch_class(n_tot, nnz_tot, K));
+    // The instances are independent, so the batch runs as kParts groups of
+    // instances of about equal site counts, each through all four steps: the
+    // upload of later groups (copy stream) and the download of the labels of
+    // earlier ones (download stream) overlap the labelling of a group (the
+    // caller's stream), and uploads and downloads use the two directions of
+    // the link at once.
+    constexpr int kParts = (int)(sizeof(ctx->bh_up) / sizeof(ctx->bh_up[0]));
+    int32_t kb[kParts + 1];
+    kb[0] = 0;
+    kb[kParts] = K;
+    for (int part = 1; part < kParts; ++part) {
+        const int64_t target = n_tot * part / kParts;
+        const int32_t k = (int32_t)(std::upper_bound(site_off, site_off + K + 1, target) - site_off - 1);
+        kb[part] = std::min(K, std::max(k, kb[part - 1]));
+    }
     // the uploads may not overwrite the buffers before earlier work on s is done
-    CCL_CUDA(cudaEventRecord(ctx->part_ev[kHostParts], s));
-    CCL_CUDA(cudaStreamWaitEvent(ctx->copy_stream, ctx->part_ev[kHostParts], 0));
-    // all bit words first (nnz/8 bytes), then the rows and columns of the
-    // instances in kHostParts groups of about equal site counts; step (i) on a
-    // group starts when its rows and columns have arrived
-    if (b_bits) CCL_CUDA(cudaMemcpyAsync(d_bits, bits, b_bits, cudaMemcpyHostToDevice, ctx->copy_stream));
-    int32_t band_off = 0;
-    int32_t k0 = 0;
-    for (int part = 0; part < kHostParts; ++part) {
-        int32_t k1 = K;
-        if (part + 1 < kHostParts) {
-            const int64_t target = n_tot * (part + 1) / kHostParts;
-            k1 = (int32_t)(std::upper_bound(site_off, site_off + K + 1, target) - site_off - 1);
-            k1 = std::max(k1, k0);
-        }
+    CCL_CUDA(cudaEventRecord(ctx->bh_done[kParts], s));
+    CCL_CUDA(cudaStreamWaitEvent(ctx->copy_stream, ctx->bh_done[kParts], 0));
+    CCL_CUDA(cudaStreamWaitEvent(ctx->d2h_stream, ctx->bh_done[kParts], 0));
+    for (int part = 0; part < kParts; ++part) {
+        const int32_t k0 = kb[part], k1 = kb[part + 1];
         const int64_t r0 = site_off[k0] + k0, r1 = site_off[k1] + k1;    // row pointers of instances [k0, k1)
         const int64_t e0 = ent_off[k0], e1 = ent_off[k1];
         if (r1 > r0)
             CCL_CUDA(cudaMemcpyAsync(d_rp + r0, row_ptr + r0, (size_t)(r1 - r0) * 4, cudaMemcpyHostToDevice,
                                      ctx->copy_stream));
-        if (e1 > e0)
+        if (e1 > e0) {
             CCL_CUDA(cudaMemcpyAsync(d_ci + e0, col_idx + e0, (size_t)(e1 - e0) * 4, cudaMemcpyHostToDevice,
                                      ctx->copy_stream));
-        CCL_CUDA(cudaEventRecord(ctx->part_ev[part], ctx->copy_stream));
-        CCL_CUDA(cudaStreamWaitEvent(s, ctx->part_ev[part], 0));
-        const int64_t t0 = k0 < K ? table[(size_t)k0].tile_begin : tiles;
-        const int64_t t1 = k1 < K ? table[(size_t)k1].tile_begin : tiles;
-        if (t1 > t0) {
-            P.tile_off = t0;
-            P.n_tiles = t1 - t0;
-            P.band_off = band_off;
-            const int64_t g = init_grid(ctx, P, batched, kMaxBands / kHostParts);
-            st = launch_init(P, batched, g, s);
-            if (st != CCL_OK) return st;
-            band_off += (int32_t)g;
+            const int64_t w0 = e0 >> 5, w1 = ((e1 - 1) >> 5) + 1;    // a word shared by two groups comes twice
+            CCL_CUDA(cudaMemcpyAsync(d_bits + w0, bits + w0, (size_t)(w1 - w0) * 4, cudaMemcpyHostToDevice,
+                                     ctx->copy_stream));
         }
-        k0 = k1;
+        CCL_CUDA(cudaEventRecord(ctx->bh_up[part], ctx->copy_stream));
     }
-    P.tile_off = 0;
-    P.n_tiles = tiles;
-    P.band_off = 0;
-    P.n_bands = band_off;
-    st = enqueue_tail(ctx, P, batched, tc, s, false);
-    if (st != CCL_OK) return st;
+    // the statistics counters add up over the groups
+    CCL_CUDA(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), s));
+    std::vector<Inst> tg;
+    for (int part = 0; part < kParts; ++part) {
+        const int32_t k0 = kb[part], k1 = kb[part + 1];
+        const int64_t c0 = k0 < K ? table[(size_t)k0].chunk_begin : chunks;
+        const int64_t c1 = k1 < K ? table[(size_t)k1].chunk_begin : chunks;
+        if (c1 == c0) continue;                 // no sites in this group
+        const int64_t t0 = table[(size_t)k0].tile_begin;
+        const int64_t t1 = k1 < K ? table[(size_t)k1].tile_begin : tiles;
+        // the group's entries of the batch table, chunk, tile and queue
+        // offsets counted from the group's first instance (pointers, bit
+        // offsets and copy bounds stay those of the whole batch)
+        tg.assign(table.begin() + k0, table.begin() + k1);
+        for (Inst &I : tg) {
+            I.chunk_begin -= c0;
+            I.tile_begin -= t0;
+            I.q_off -= ent_off[k0];
+        }
+        const bool bat = k1 - k0 > 1;
+        Params P = base_params(ctx, tc);
+        P.K = k1 - k0;
+        P.n_chunks = c1 - c0;
+        if (bat) {
+            st = upload_table(ctx, tg, s);
+            if (st != CCL_OK) return st;
+            P.insts = ctx->d_insts;
+        } else {
+            P.one = tg[0];
+        }
+        CCL_CUDA(cudaMemsetAsync(P.band, 0, (size_t)kMaxBands * sizeof(BandRec), s));
+        CCL_CUDA(cudaStreamWaitEvent(s, ctx->bh_up[part], 0));
+        P.tile_off = 0;
+        P.n_tiles = t1 - t0;
+        P.band_off = 0;
+        const int64_t g = init_grid(ctx, P, bat, kMaxBands);
+        st = launch_init(P, bat, g, s);
+        if (st != CCL_OK) return st;
+        P.n_bands = (int32_t)g;
+        st = enqueue_tail(ctx, P, bat, tc, s, false);
+        if (st != CCL_OK) return st;
+        CCL_CUDA(cudaEventRecord(ctx->bh_done[part], s));
+        CCL_CUDA(cudaStreamWaitEvent(ctx->d2h_stream, ctx->bh_done[part], 0));
+        CCL_CUDA(cudaMemcpyAsync(labels + site_off[k0], d_lab + site_off[k0],
+                                 (size_t)(site_off[k1] - site_off[k0]) * 4, cudaMemcpyDeviceToHost,
+                                 ctx->d2h_stream));
+    }
     CCL_CUDA(cudaEventRecord(ctx->stats_ev, s));
-    CCL_CUDA(cudaMemcpyAsync(labels, d_lab, b_lab, cudaMemcpyDeviceToHost, s));
+    // later work on s (and ccl_sync) comes after the downloads
+    CCL_CUDA(cudaEventRecord(ctx->bh_done[kParts], ctx->d2h_stream));
+    CCL_CUDA(cudaStreamWaitEvent(s, ctx->bh_done[kParts], 0));
+    ctx->last.n_inst = K;
+    ctx->last.n_sites = n_tot;
+    ctx->last.nnz = nnz_tot;
     return ccl_sync(ctx, stream, -1);
 }
 
