@@ -225,6 +225,9 @@ __device__ __forceinline__ void init_produce(const Params &P, Stage *st, uint64_
         h.e0 = __ldcs(I.row_ptr + h.s0);
         h.e1 = __ldcs(I.row_ptr + h.s0 + h.ts);
         h.status = (h.e0 < 0 || h.e1 < h.e0 || h.e1 > I.nnz) ? 1 : 0;
+        // row_ptr[0] == 0 and row_ptr[n] == nnz, once per instance
+        if (h.s0 == 0 && h.e0 != 0) raise_err(P.err, kErrShape);
+        if (h.s0 + h.ts == I.n && h.e1 != I.nnz) raise_err(P.err, kErrShape);
         h.i_rp = I.row_ptr;
         h.i_ci = I.col_idx;
         h.i_bits = I.bits;
@@ -597,11 +600,6 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
         }
         const Stage &S = st[s];
         const Inst I = stage_inst<kBatched>(P, S.h);
-        if (lane == 0 && warp == 0) {
-            // row_ptr[0] == 0 and row_ptr[n] == nnz, once per instance
-            if (S.h.s0 == 0 && S.h.e0 != 0) raise_err(P.err, kErrShape);
-            if (S.h.s0 + S.h.ts == I.n && S.h.e1 != I.nnz) raise_err(P.err, kErrShape);
-        }
         TileCtx tc;
         tc.rb0 = S.h.t_rb0;
         tc.nbits = S.h.t_nbits;
