@@ -319,6 +319,22 @@ struct TileCtx {
     bool staged;        // the stage holds the columns and bits of the tile's whole entry range
 };
 
+// The stage header words the register path reads, copied to registers once
+// per tile with 16-byte shared-memory loads.
+struct TileHdr {
+    int32_t k, s0, ts, e0, e1, rp_lo, rp_hi, ci_lo;
+};
+
+__device__ __forceinline__ void load_tile_hdr(const StageHdr &h, TileHdr &th, TileCtx &tc) {
+    const int4 a = *reinterpret_cast<const int4 *>(&h.k);
+    const int4 b = *reinterpret_cast<const int4 *>(&h.e1);
+    const int4 c = *reinterpret_cast<const int4 *>(&h.t_rb0);
+    th.k = a.x; th.s0 = a.y; th.ts = a.z; th.e0 = a.w;
+    th.e1 = b.x; th.rp_lo = b.y; th.rp_hi = b.z; th.ci_lo = b.w;
+    tc.rb0 = c.x; tc.nbits = c.y; tc.staged = c.z != 0; tc.vis_lo = c.w;
+    tc.vis_hi = h.t_vis_hi;
+}
+
 // One chunk of 32 sites. The tiles of this CTA's band that were finished at
 // least kStages tiles ago are visible (their labels were released through the
 // stage barriers): a site whose smallest open lower neighbour m lies in such
@@ -417,8 +433,8 @@ __device__ __forceinline__ void init_scan_chunk(const Params &P, const Stage &S,
 // false (having done nothing) otherwise.
 template <bool kBatched, bool kGen = false>
 __device__ __forceinline__ bool init_scan_pair(const Params &P, const Stage &S, const Inst &I, int cc0,
-                                               int lane, const TileCtx &tc, ChunkRes &c0, ChunkRes &c1) {
-    const StageHdr &h = S.h;
+                                               int lane, const TileCtx &tc, const TileHdr &h, ChunkRes &c0,
+                                               ChunkRes &c1) {
     const int32_t n = I.n;
     const int32_t s00 = h.s0 + cc0 * kChunk;
     if (!tc.staged || s00 + 2 * kChunk > n || s00 < h.rp_lo || s00 + 2 * kChunk >= h.rp_hi) return false;
@@ -538,9 +554,8 @@ __device__ __forceinline__ void init_emit_chunk(const Params &P, const Stage &S,
 // warp-uniform trip count, so the warp neither diverges nor loops twice.
 // The queue order is that of init_emit_chunk on chunk 0 then chunk 1.
 template <bool kBatched>
-__device__ __forceinline__ void init_emit_pair(const Params &P, const Stage &S, const ChunkRes &c0,
-                                               const ChunkRes &c1, int64_t slot, int rr) {
-    const StageHdr &h = S.h;
+__device__ __forceinline__ void init_emit_pair(const Params &P, const Stage &S, const TileHdr &h,
+                                               const ChunkRes &c0, const ChunkRes &c1, int64_t slot, int rr) {
     const int iters = (int)__reduce_max_sync(kFull, (uint32_t)rr);
     uint32_t mm = c0.resmask | (c1.resmask << 16);
     if (slot + rr > P.q_cap) {                  // corrupt rows only
@@ -601,11 +616,8 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
         const Stage &S = st[s];
         const Inst I = stage_inst<kBatched>(P, S.h);
         TileCtx tc;
-        tc.rb0 = S.h.t_rb0;
-        tc.nbits = S.h.t_nbits;
-        tc.staged = S.h.t_staged != 0;
-        tc.vis_lo = S.h.t_vis_lo;
-        tc.vis_hi = S.h.t_vis_hi;
+        TileHdr th;
+        load_tile_hdr(S.h, th, tc);
         static_assert(kChunksPerConsumer == 2, "a consumer warp scans two chunks per tile");
         {
             // both chunks are scanned first; their pairs then take one range of
@@ -615,8 +627,8 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
             c0.r = c1.r = 0;
             c0.resmask = c1.resmask = 0u;
             c0.fast = c1.fast = true;
-            const bool has0 = cc0 * kChunk < S.h.ts, has1 = cc1 * kChunk < S.h.ts;
-            if (!(has1 && init_scan_pair<kBatched, kGen>(P, S, I, cc0, lane, tc, c0, c1))) {
+            const bool has0 = cc0 * kChunk < th.ts, has1 = cc1 * kChunk < th.ts;
+            if (!(has1 && init_scan_pair<kBatched, kGen>(P, S, I, cc0, lane, tc, th, c0, c1))) {
                 if (has0) init_scan_chunk<kBatched, kGen>(P, S, I, cc0, lane, tc, c0);
                 if (has1) init_scan_chunk<kBatched, kGen>(P, S, I, cc1, lane, tc, c1);
             }
@@ -636,7 +648,7 @@ __global__ void __launch_bounds__(kInitThreads, 2) k_init(Params P) {
                 if (lane == 0) my_pairs += (unsigned long long)total;
                 const int64_t slot = S.h.qband + (int64_t)base + (incl - rr);
                 if (c0.fast && c1.fast) {
-                    init_emit_pair<kBatched>(P, S, c0, c1, slot, rr);
+                    init_emit_pair<kBatched>(P, S, th, c0, c1, slot, rr);
                 } else {
                     if (c0.r > 0) init_emit_chunk<kBatched, kGen>(P, S, I, c0, slot);
                     if (c1.r > 0) init_emit_chunk<kBatched, kGen>(P, S, I, c1, slot + c0.r);

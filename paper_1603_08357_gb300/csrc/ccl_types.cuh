@@ -2,6 +2,7 @@
 // per-instance descriptor, the per-chunk record and the kernel parameters.
 #pragma once
 #include <stdint.h>
+#include <stddef.h>
 #include <cuda_runtime.h>
 
 namespace ccl {
@@ -121,6 +122,21 @@ struct __align__(16) StageHdr {
     // [vis_lo, vis_hi] of the band whose labels are final and visible
     int32_t t_rb0, t_nbits, t_staged, t_vis_lo, t_vis_hi, pad2_;
 };
+
+// the consumers load {k, s0, ts, e0}, {e1, rp_lo, rp_hi, ci_lo} and {t_rb0,
+// t_nbits, t_staged, t_vis_lo} as one 16-byte word each
+static_assert(offsetof(StageHdr, k) % 16 == 0 && offsetof(StageHdr, s0) == offsetof(StageHdr, k) + 4 &&
+                  offsetof(StageHdr, ts) == offsetof(StageHdr, k) + 8 &&
+                  offsetof(StageHdr, e0) == offsetof(StageHdr, k) + 12 &&
+                  offsetof(StageHdr, e1) == offsetof(StageHdr, k) + 16 &&
+                  offsetof(StageHdr, rp_lo) == offsetof(StageHdr, k) + 20 &&
+                  offsetof(StageHdr, rp_hi) == offsetof(StageHdr, k) + 24 &&
+                  offsetof(StageHdr, ci_lo) == offsetof(StageHdr, k) + 28,
+              "stage header words read as int4");
+static_assert(offsetof(StageHdr, t_rb0) % 16 == 0 && offsetof(StageHdr, t_nbits) == offsetof(StageHdr, t_rb0) + 4 &&
+                  offsetof(StageHdr, t_staged) == offsetof(StageHdr, t_rb0) + 8 &&
+                  offsetof(StageHdr, t_vis_lo) == offsetof(StageHdr, t_rb0) + 12,
+              "stage header tile words read as int4");
 
 struct __align__(16) Stage {
     StageHdr h;
