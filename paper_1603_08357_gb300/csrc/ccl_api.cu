@@ -1260,7 +1260,7 @@ ccl_status ccl_sync(ccl_context *ctx, void *stream, int64_t timeout_ms) {
 }
 
 namespace {
-constexpr int kHostParts = 4;        // upload parts of the host-buffer path
+constexpr int kHostParts = 4;        // upload parts of the single-instance host-buffer path
 
 // The host-buffer path for inputs of at least 64 tiles: the input goes up in
 // kHostParts site ranges on the copy stream, and step (i) on each range starts

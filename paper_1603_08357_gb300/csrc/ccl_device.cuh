@@ -17,8 +17,8 @@
 //    pairs with kRedSlots (six) pairs per lane in lockstep rounds (one load
 //    or atomicMin per live pair per round, next state from a small table).
 //  * Steps (ii)/(iv) chase every site's chain to its root, two chains per
-//    lane at once, each warp over a contiguous range of sites (or
-//    interleaved, for inputs without locality).
+//    lane at once (four in a batch), each warp over a contiguous range of
+//    sites (or interleaved, for inputs without locality).
 #pragma once
 #include <stdint.h>
 #include <cuda_runtime.h>
