@@ -290,8 +290,11 @@ def test_batched_matches_oracle_and_single(ctx, graphs):
 @pytest.mark.parametrize("K", [1, 3, 150])
 def test_batched_host_path(ctx, K):
     """ccl_label_batched_host: host arrays in, labels out, the instances
-    uploaded in four groups with step (i) started per group; equal to the
-    oracle and to the device-array call, twice in a row (buffers reused)."""
+    labelled in groups, each through all four steps, with the label downloads
+    of earlier groups overlapping the uploads of later ones (K = 1: one group;
+    K = 3: empty groups, one-instance groups and an empty instance); equal to
+    the oracle and to the device-array call, twice in a row (buffers reused),
+    and the statistics count the residual pairs of every group."""
     specs = _mixed_specs(K, 40 + K)
     if K == 3:
         specs[1] = dict(kind="triangle", L=0, p=0.5, seed=1)     # an empty instance in the middle
@@ -303,6 +306,9 @@ def test_batched_host_path(ctx, K):
                                         b.open_bits, out)
         assert st == ccl.CCL_OK, ccl.ccl_status_string(st)
         assert np.array_equal(out, want)
+    stats = ccl.ccl_get_stats(ctx)
+    assert stats.n_inst == b.k and stats.n_sites == b.n_total
+    assert stats.residual_pairs == sum(oracle.steps_label(L.make_instance(sp))["n_residual"] for sp in specs)
     assert np.array_equal(gpu_label_batched(ctx, b), want)
     assert ccl.ccl_get_stats(ctx).n_inst == b.k
 
