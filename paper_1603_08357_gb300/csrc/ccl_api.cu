@@ -1469,6 +1469,13 @@ ccl_status ccl_label_batched_host(ccl_context *ctx, int32_t K, const int64_t *si
     }
     // the statistics counters add up over the groups
     CCL_CUDA(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(unsigned long long), s));
+    // an error after the first download was queued: wait for the downloads
+    // already queued, so none writes into `labels` after the return
+    auto fail = [&](ccl_status e) {
+        (void)cudaStreamSynchronize(ctx->d2h_stream);
+        (void)cudaGetLastError();
+        return e;
+    };
     std::vector<Inst> tg;
     for (int part = 0; part < kParts; ++part) {
         const int32_t k0 = kb[part], k1 = kb[part + 1];
@@ -1492,32 +1499,34 @@ ccl_status ccl_label_batched_host(ccl_context *ctx, int32_t K, const int64_t *si
         P.n_chunks = c1 - c0;
         if (bat) {
             st = upload_table(ctx, tg, s);
-            if (st != CCL_OK) return st;
+            if (st != CCL_OK) return fail(st);
             P.insts = ctx->d_insts;
         } else {
             P.one = tg[0];
         }
-        CCL_CUDA(cudaMemsetAsync(P.band, 0, (size_t)kMaxBands * sizeof(BandRec), s));
-        CCL_CUDA(cudaStreamWaitEvent(s, ctx->bh_up[part], 0));
+        if (cudaMemsetAsync(P.band, 0, (size_t)kMaxBands * sizeof(BandRec), s) != cudaSuccess ||
+            cudaStreamWaitEvent(s, ctx->bh_up[part], 0) != cudaSuccess)
+            return fail(CCL_ERR_CUDA);
         P.tile_off = 0;
         P.n_tiles = t1 - t0;
         P.band_off = 0;
         const int64_t g = init_grid(ctx, P, bat, kMaxBands);
         st = launch_init(P, bat, g, s);
-        if (st != CCL_OK) return st;
+        if (st != CCL_OK) return fail(st);
         P.n_bands = (int32_t)g;
         st = enqueue_tail(ctx, P, bat, tc, s, false);
-        if (st != CCL_OK) return st;
-        CCL_CUDA(cudaEventRecord(ctx->bh_done[part], s));
-        CCL_CUDA(cudaStreamWaitEvent(ctx->d2h_stream, ctx->bh_done[part], 0));
-        CCL_CUDA(cudaMemcpyAsync(labels + site_off[k0], d_lab + site_off[k0],
-                                 (size_t)(site_off[k1] - site_off[k0]) * 4, cudaMemcpyDeviceToHost,
-                                 ctx->d2h_stream));
+        if (st != CCL_OK) return fail(st);
+        if (cudaEventRecord(ctx->bh_done[part], s) != cudaSuccess ||
+            cudaStreamWaitEvent(ctx->d2h_stream, ctx->bh_done[part], 0) != cudaSuccess ||
+            cudaMemcpyAsync(labels + site_off[k0], d_lab + site_off[k0], (size_t)(site_off[k1] - site_off[k0]) * 4,
+                            cudaMemcpyDeviceToHost, ctx->d2h_stream) != cudaSuccess)
+            return fail(CCL_ERR_CUDA);
     }
-    CCL_CUDA(cudaEventRecord(ctx->stats_ev, s));
     // later work on s (and ccl_sync) comes after the downloads
-    CCL_CUDA(cudaEventRecord(ctx->bh_done[kParts], ctx->d2h_stream));
-    CCL_CUDA(cudaStreamWaitEvent(s, ctx->bh_done[kParts], 0));
+    if (cudaEventRecord(ctx->stats_ev, s) != cudaSuccess ||
+        cudaEventRecord(ctx->bh_done[kParts], ctx->d2h_stream) != cudaSuccess ||
+        cudaStreamWaitEvent(s, ctx->bh_done[kParts], 0) != cudaSuccess)
+        return fail(CCL_ERR_CUDA);
     ctx->last.n_inst = K;
     ctx->last.n_sites = n_tot;
     ctx->last.nnz = nnz_tot;
